@@ -1,0 +1,227 @@
+"""FP64 CPU oracle of the coupled central-moment LBM (test infrastructure).
+
+Only the tests, ``__graft_entry__.smoke()`` and the bench's CPU-baseline leg
+may import this package.  The product path (``paper_2504_09024_gb300``) never
+imports it and shares no code with it.
+
+The C source ``lbm_oracle.c`` computes each collision with the literal 9x9
+matrices of the paper (P and P^-1 of App. A; F(u), F^-1(u) generated from the
+binomial definition, Eq. cmscalar; B and B^-1 of App. D) in the order of the
+algorithm lists of Sec. 3, App. C and App. D.  ``mlp.py`` holds the FP64
+reference of the surrogate network.
+
+Parity status of each function is recorded in the repository's design notes;
+the pins live in ``tests/test_oracle_pins.py``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIBDIR = os.path.join(_HERE, "_lib")
+_SO = os.path.join(_LIBDIR, "liblbm_oracle.so")
+_SRC = [os.path.join(_HERE, "lbm_oracle.c")]
+_HDR = os.path.join(_HERE, "lbm_oracle.h")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False, openmp: bool = True) -> str:
+    """Compile the oracle with gcc into oracle/_lib/liblbm_oracle.so."""
+    os.makedirs(_LIBDIR, exist_ok=True)
+    newest = max(os.path.getmtime(p) for p in _SRC + [_HDR])
+    if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= newest:
+        return _SO
+    tmp = _SO + f".tmp{os.getpid()}"
+    base = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp] + _SRC + ["-lm"]
+    cmds = [base[:1] + ["-fopenmp"] + base[1:]] if openmp else []
+    cmds.append(base)
+    err = None
+    for cmd in cmds:
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode == 0:
+            os.replace(tmp, _SO)
+            return _SO
+        err = r.stderr
+    raise RuntimeError(f"oracle build failed:\n{err}")
+
+
+class OrcParams(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("walls_y", ctypes.c_int),
+        ("mode", ctypes.c_int), ("sigma_literal", ctypes.c_int), ("pad_", ctypes.c_int),
+        ("u_wall", ctypes.c_double), ("W", ctypes.c_double), ("phi_a", ctypes.c_double),
+        ("phi_b", ctypes.c_double), ("M_phi", ctypes.c_double), ("D_s", ctypes.c_double),
+        ("nu_a", ctypes.c_double), ("nu_b", ctypes.c_double), ("zeta", ctypes.c_double),
+        ("rho_a", ctypes.c_double), ("rho_b", ctypes.c_double), ("sigma_o", ctypes.c_double),
+        ("beta", ctypes.c_double), ("c_max", ctypes.c_double), ("fext_x", ctypes.c_double),
+        ("fext_y", ctypes.c_double),
+    ]
+
+
+class OrcDiag(ctypes.Structure):
+    _fields_ = [
+        ("step", ctypes.c_longlong), ("sum_phi", ctypes.c_double), ("sum_c", ctypes.c_double),
+        ("D", ctypes.c_double), ("L", ctypes.c_double), ("B", ctypes.c_double),
+        ("xc", ctypes.c_double), ("yc", ctypes.c_double), ("umax", ctypes.c_double),
+        ("nonfinite", ctypes.c_longlong), ("sigma_neg", ctypes.c_longlong),
+    ]
+
+
+_DP = ctypes.POINTER(ctypes.c_double)
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = build()
+            L = ctypes.CDLL(path)
+            L.orc_create.restype = ctypes.c_void_p
+            L.orc_create.argtypes = [ctypes.POINTER(OrcParams)]
+            L.orc_destroy.argtypes = [ctypes.c_void_p]
+            L.orc_init.argtypes = [ctypes.c_void_p] + [_DP] * 5
+            L.orc_step.argtypes = [ctypes.c_void_p, ctypes.c_int]
+            L.orc_get_step.restype = ctypes.c_longlong
+            L.orc_get_step.argtypes = [ctypes.c_void_p]
+            L.orc_fields.argtypes = [ctypes.c_void_p] + [_DP] * 5
+            L.orc_geometry.argtypes = [ctypes.c_void_p] + [_DP] * 6
+            L.orc_get_pops.argtypes = [ctypes.c_void_p] + [_DP] * 3
+            L.orc_set_pops.argtypes = [ctypes.c_void_p] + [_DP] * 3
+            L.orc_set_velocity.argtypes = [ctypes.c_void_p] + [_DP] * 2
+            L.orc_reset_f.argtypes = [ctypes.c_void_p, _DP]
+            L.orc_diagnostics.argtypes = [ctypes.c_void_p, ctypes.POINTER(OrcDiag)]
+            L.orc_matrix_P.argtypes = [_DP]
+            L.orc_matrix_Pinv.argtypes = [_DP]
+            L.orc_matrix_F.argtypes = [ctypes.c_double, ctypes.c_double, _DP]
+            L.orc_matrix_Finv.argtypes = [ctypes.c_double, ctypes.c_double, _DP]
+            L.orc_gradient.argtypes = [ctypes.c_void_p, _DP, _DP, _DP]
+            L.orc_num_threads.restype = ctypes.c_int
+            _lib = L
+    return _lib
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(_DP)
+
+
+def _arr(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+
+
+def params_from(phys) -> OrcParams:
+    d = phys.as_dict() if hasattr(phys, "as_dict") else dict(phys)
+    p = OrcParams()
+    for name, _ in OrcParams._fields_:
+        if name in d:
+            setattr(p, name, d[name])
+    return p
+
+
+def matrix(name, ux=0.0, uy=0.0):
+    out = np.zeros(81)
+    L = lib()
+    if name == "P":
+        L.orc_matrix_P(_ptr(out))
+    elif name == "Pinv":
+        L.orc_matrix_Pinv(_ptr(out))
+    elif name == "F":
+        L.orc_matrix_F(ux, uy, _ptr(out))
+    elif name == "Finv":
+        L.orc_matrix_Finv(ux, uy, _ptr(out))
+    else:
+        raise ValueError(name)
+    return out.reshape(9, 9)
+
+
+def num_threads() -> int:
+    return lib().orc_num_threads()
+
+
+class Sim:
+    """One oracle run.  Fields are [ny][nx] float64; populations [9][ny][nx]."""
+
+    def __init__(self, phys):
+        self.phys = phys
+        self.nx, self.ny = int(phys.nx), int(phys.ny)
+        self._p = params_from(phys)
+        self._h = lib().orc_create(ctypes.byref(self._p))
+        if not self._h:
+            raise ValueError("oracle: invalid parameters")
+
+    def close(self):
+        if self._h:
+            lib().orc_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init(self, phi, c, ux, uy, P=None):
+        a = [_arr(v) for v in (phi, c, ux, uy, P)]
+        lib().orc_init(self._h, *[_ptr(v) for v in a])
+
+    def step(self, n=1):
+        lib().orc_step(self._h, int(n))
+
+    @property
+    def t(self):
+        return lib().orc_get_step(self._h)
+
+    def fields(self):
+        out = [np.zeros((self.ny, self.nx)) for _ in range(5)]
+        lib().orc_fields(self._h, *[_ptr(v) for v in out])
+        return dict(zip(("phi", "c", "ux", "uy", "P"), out))
+
+    def geometry(self):
+        out = [np.zeros((self.ny, self.nx)) for _ in range(6)]
+        lib().orc_geometry(self._h, *[_ptr(v) for v in out])
+        return dict(zip(("nx", "ny", "gmag", "kappa", "Fsx", "Fsy"), out))
+
+    def pops(self):
+        out = [np.zeros((9, self.ny, self.nx)) for _ in range(3)]
+        lib().orc_get_pops(self._h, *[_ptr(v) for v in out])
+        return dict(zip(("f", "h", "g"), out))
+
+    def set_pops(self, f=None, h=None, g=None):
+        a = [_arr(v) for v in (f, h, g)]
+        lib().orc_set_pops(self._h, *[_ptr(v) for v in a])
+
+    def set_velocity(self, ux, uy):
+        a = [_arr(v) for v in (ux, uy)]
+        lib().orc_set_velocity(self._h, *[_ptr(v) for v in a])
+
+    def reset_f(self, phi):
+        a = _arr(phi)
+        lib().orc_reset_f(self._h, _ptr(a))
+
+    def gradient(self, field):
+        a = _arr(field)
+        gx = np.zeros_like(a)
+        gy = np.zeros_like(a)
+        lib().orc_gradient(self._h, _ptr(a), _ptr(gx), _ptr(gy))
+        return gx, gy
+
+    def diagnostics(self):
+        d = OrcDiag()
+        lib().orc_diagnostics(self._h, ctypes.byref(d))
+        return {name: getattr(d, name) for name, _ in OrcDiag._fields_}
+
+
+def run_case(case, steps=None):
+    """Convenience: build, initialise and advance an oracle run of a workload Case."""
+    s = Sim(case.phys)
+    s.init(case.phi, case.c, case.ux, case.uy, case.P)
+    s.step(case.steps if steps is None else steps)
+    return s
