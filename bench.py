@@ -1,0 +1,344 @@
+"""Throughput of the coupled three-lattice step (MLUPS) on GB300.
+
+Default workload: the 2048x1024 drop-in-shear grid (R = 192, W = 5, Ca = 0.1,
+beta = 0.3, Gamma0 = 0.3, Re = 0.1, Pe_s = 10), FP32 populations, coupled
+f + h + g lattices with moving walls.  One bench step = one LBM time step of
+the whole grid (one fused kernel launch).  The population buffers (453 MB)
+exceed L2, so no explicit flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle on the host cores instead (each
+step a bounded window of the same workload).  Under torchrun (N > 1) every
+rank runs an independent replica (the single-grid path has no exchange step);
+value = total cell updates of all ranks / max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+BYTES_PER_CELL = {"f32": 216, "f16s": 124, "bf16s": 124}  # algorithmic bytes per coupled cell update
+METRIC = "coupled MLUPS"
+UNIT = "MLUPS"
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.remove(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def make_case(name):
+    from paper_2504_09024_gb300 import workloads as W
+    if name == "2048x1024":
+        return W.shear_drop_2048x1024(Ca=0.1)
+    if name == "512x256":
+        return W.shear_drop_512x256()
+    raise SystemExit(f"unknown workload {name}")
+
+
+def traffic_record(kernel_name):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on
+    the current kernel source (hash match); else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        rec = json.load(open(path)).get(kernel_name)
+    except Exception:
+        return None
+    if not rec:
+        return None
+    from paper_2504_09024_gb300 import build as B
+    if rec.get("source_hash") != B.source_hash():
+        return None
+    return rec
+
+
+def cpu_baseline(case, budget_s=15.0):
+    """FP64 oracle on the host cores over a bounded window of the workload."""
+    import oracle
+    from paper_2504_09024_gb300 import workloads as W
+    nx, ny = case.phys.nx, case.phys.ny
+    # window: full height band through the drop centre, width chosen by a probe
+    def window(wx, wy):
+        x0 = int(max(0, nx // 2 - int(case.meta.get("R", 0)) - wx // 2))
+        x0 = min(x0, nx - wx)
+        y0 = (ny - wy) // 2
+        sl = (slice(y0, y0 + wy), slice(x0, x0 + wx))
+        phys = W.Physics(**{**case.phys.as_dict(), "nx": wx, "ny": wy})
+        return phys, [a[sl].copy() for a in (case.phi, case.c, case.ux, case.uy)]
+
+    phys, arrs = window(min(nx, 256), min(ny, 128))
+    s = oracle.Sim(phys)
+    s.init(*arrs)
+    s.step(1)
+    t0 = time.perf_counter()
+    s.step(2)
+    per_cell_step = (time.perf_counter() - t0) / (2 * phys.nx * phys.ny)
+    s.close()
+    steps = max(1, int(budget_s / (per_cell_step * phys.nx * phys.ny)))
+    s = oracle.Sim(phys)
+    s.init(*arrs)
+    t0 = time.perf_counter()
+    s.step(steps)
+    dt = time.perf_counter() - t0
+    s.close()
+    mlups = phys.nx * phys.ny * steps / dt / 1e6
+    return {"value": mlups, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{steps} steps of a {phys.nx}x{phys.ny} window of the {nx}x{ny} "
+                      f"workload through the drop interface ({dt:.1f} s)"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    case = make_case(args.workload)
+    from paper_2504_09024_gb300 import workloads as W
+    nx, ny = case.phys.nx, case.phys.ny
+    total_steps = args.steps + args.warmup
+    # size the per-step window so the whole run takes about args.ref_budget seconds
+    probe = W.Physics(**{**case.phys.as_dict(), "nx": 128, "ny": 64})
+    s = oracle.Sim(probe)
+    s.init(*(a[(ny - 64) // 2:(ny + 64) // 2, :128].copy() for a in (case.phi, case.c, case.ux, case.uy)))
+    s.step(1)
+    t0 = time.perf_counter()
+    s.step(3)
+    t_cell = (time.perf_counter() - t0) / (3 * 128 * 64)
+    s.close()
+    cells = max(64, min(nx * ny, int(args.ref_budget / (total_steps * t_cell))))
+    wy = max(4, min(ny, int(math.sqrt(cells / 2))))
+    wx = max(4, min(nx, cells // wy))
+    y0, x0 = (ny - wy) // 2, max(0, (nx - wx) // 2)
+    sl = (slice(y0, y0 + wy), slice(x0, x0 + wx))
+    phys = W.Physics(**{**case.phys.as_dict(), "nx": wx, "ny": wy})
+    s = oracle.Sim(phys)
+    s.init(*(a[sl].copy() for a in (case.phi, case.c, case.ux, case.uy)))
+    s.step(args.warmup)
+    t0 = time.perf_counter()
+    s.step(args.steps)
+    dt = time.perf_counter() - t0
+    s.close()
+    value = wx * wy * args.steps / dt / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": case.name, "grid": f"{nx}x{ny}",
+                   "sample": f"{wx}x{wy} window per step", "parallelism": "host threads"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(),
+                         "kind": "oracle",
+                         "sample": f"each step: one oracle step of a {wx}x{wy} window of the "
+                                   f"{nx}x{ny} workload"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_2504_09024_gb300 import lbm
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist  # noqa: F811
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    case = make_case(args.workload)
+    nx, ny = case.phys.nx, case.phys.ny
+    ncell = nx * ny
+    dtype_code = {"f32": lbm.LBM_F32, "f16s": lbm.LBM_F16S, "bf16s": lbm.LBM_BF16S}[args.dtype]
+    kern = {"auto": lbm.LBM_KERNEL_AUTO, "fused": lbm.LBM_KERNEL_FUSED,
+            "split": lbm.LBM_KERNEL_SPLIT}[args.kernel]
+    stream = torch.cuda.Stream()
+    sim = lbm.Sim(case.phys, dtype=dtype_code, kernel=kern, stream=stream.cuda_stream)
+    if args.tile_x or args.seg_y:
+        sim.set_launch_shape(args.tile_x, args.seg_y)
+    sim.init(case.phi, case.c, case.ux, case.uy)
+    launches = lbm.lbm_launches_per_step(sim.ctx)
+
+    # warm-up (also captures the CUDA graphs)
+    sim.step(args.warmup)
+    sim.sync()
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.step(args.steps)
+    e1.record(stream)
+    e1.synchronize()
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = world * ncell * args.steps / (ms_max * 1e-3) / 1e6
+    ms_step = ms_max / args.steps
+
+    # end-to-end through the public API with pinned host buffers: initialise
+    # from host fields, run the same number of steps, read fields + diagnostics
+    host_in = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+               for a in (case.phi, case.c, case.ux, case.uy)]
+    host_out = [torch.empty((ny, nx), dtype=torch.float64).pin_memory() for _ in range(5)]
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lbm.lbm_init_fields(sim.ctx, *host_in)
+    sim.step(args.steps)
+    lbm.lbm_get_fields(sim.ctx, *host_out)
+    diag = sim.diagnostics()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    e2e_s = float(t.item())
+    h2d = sum(a.numel() * 8 for a in host_in)
+    d2h = sum(a.numel() * 8 for a in host_out) + 128
+
+    peak, peak_kind = peaks()
+    bpc = BYTES_PER_CELL[args.dtype]
+    achieved = bpc * ncell / (ms_step * 1e-3) / 1e9
+    kname = "k_fused_sweep" if lbm.lbm_kernel_in_use(sim.ctx) == lbm.LBM_KERNEL_FUSED else "k_collide"
+    tr = traffic_record(kname)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
+        "config": {"workload": case.name, "grid": f"{nx}x{ny}", "cells": ncell,
+                   "lattices": "f+h+g coupled", "kernel": kname,
+                   "launch_shape": list(lbm.lbm_get_launch_shape(sim.ctx)),
+                   "l2": "populations (2 x 226 MB) exceed the 129 MB L2; no flush",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_kind": f"{peak_kind} hbm_gbs",
+                     "bytes_per_cell": bpc,
+                     "traffic": tr["bytes_per_launch"] if tr else None},
+        "e2e": {"value": world * ncell * args.steps / e2e_s / 1e6, "unit": UNIT,
+                "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+                "what": "lbm_init_fields from pinned host fields + lbm_step(K) + lbm_get_fields "
+                        "to pinned host + lbm_diagnostics"},
+        "gpu_launches": launches * args.steps,
+        "clocks": clk,
+        "check": {"sum_phi": diag["sum_phi"], "nonfinite": diag["nonfinite"]},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(case, args.cpu_budget)
+    sim.close()
+    if rank == 0:
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20000)
+    ap.add_argument("--warmup", type=int, default=200)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="2048x1024")
+    ap.add_argument("--dtype", choices=["f32", "f16s", "bf16s"], default="f32")
+    ap.add_argument("--kernel", choices=["auto", "fused", "split"], default="auto")
+    ap.add_argument("--tile-x", type=int, default=0)
+    ap.add_argument("--seg-y", type=int, default=0)
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--ref-budget", type=float, default=90.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", args.gpus))
+    local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    return run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,203 @@
+/*
+ * lbm.h -- C ABI of liblbm.so, a GB300 (sm_103a) implementation of the
+ * coupled central-moment lattice Boltzmann method of Schupbach & Premnath,
+ * "A Robust Lattice Boltzmann Method for Interface-Bound Transport of a
+ * Passive Scalar: Application to Surfactant-Laden Multiphase Flows"
+ * (arXiv 2504.09024).
+ *
+ * One time step advances three D2Q9 lattices:
+ *   f  conservative Allen-Cahn phase field phi          (App. C, Eq. LBE_CACE)
+ *   h  interface-bound surfactant concentration c       (Sec. 3, Eq. LBE)
+ *   g  pressure-based two-fluid flow P, u, forced by the
+ *      capillary + Marangoni stress of Eq. (Fs) with the
+ *      Langmuir isotherm sigma(c) of Eq. (EOS)          (App. D, Eq. centralmomentLBE2fluidflow)
+ *
+ * Conventions shared by every entry point
+ *   - Grids are nx by ny cells; cell (i, j) has centre (i + 1/2, j + 1/2).
+ *     Host and device field arrays are row-major [ny][nx] float64, x fastest.
+ *     Population arrays are [9][ny][nx] float64 in the D2Q9 order of the
+ *     paper's P matrix (App. A): 0 (0,0) 1 (1,0) 2 (0,1) 3 (-1,0) 4 (0,-1)
+ *     5 (1,1) 6 (-1,1) 7 (-1,-1) 8 (1,-1).
+ *   - x is periodic.  y is periodic (walls_y = 0) or bounded by half-way
+ *     bounce-back walls at y = 0 and y = ny moving with -u_wall and +u_wall.
+ *   - Units are lattice units (dx = dt = 1, cs^2 = 1/3).
+ *   - The library owns all device memory of a context.  Pointers passed in
+ *     are borrowed for the duration of the call only.
+ *   - Every int-returning function returns LBM_OK (0) or a negative LBM_ERR_*
+ *     code; no exception or abort crosses the ABI.  lbm_strerror() names it.
+ *   - Work runs on the stream given to lbm_create (NULL: the library's own
+ *     non-blocking stream).  lbm_step is asynchronous; functions that return
+ *     data to the host synchronise that stream.  A CUDA error inside an
+ *     asynchronous call is reported by the next call that synchronises.
+ *   - A context is not thread-safe: calls on one context must be serialised.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBM_ABI_VERSION 1
+
+enum lbm_status {
+    LBM_OK = 0,
+    LBM_ERR_INVALID_ARG = -1,  /* bad pointer, size or parameter */
+    LBM_ERR_RATE = -2,         /* a transport coefficient gives a relaxation rate outside (0, 2) */
+    LBM_ERR_SIGMA_NEG = -3,    /* Langmuir sigma(c) < 0 for the declared concentration range */
+    LBM_ERR_CUDA = -4,         /* CUDA runtime error (device, launch, copy) */
+    LBM_ERR_NONFINITE = -5,    /* non-finite values found in fields or state */
+    LBM_ERR_TIMEOUT = -6,      /* a bounded device wait expired */
+    LBM_ERR_UNSUPPORTED = -7,  /* option not supported by this build or mode */
+    LBM_ERR_IO = -8,           /* file open/read/write failure or bad file */
+    LBM_ERR_NOMEM = -9         /* device or host allocation failed */
+};
+
+/* Storage type of the populations.  Collisions always compute in FP32. */
+enum lbm_dtype {
+    LBM_F32 = 1,    /* float32 populations; g stored as g - w_a P0 */
+    LBM_F16S = 2,   /* float16, equilibrium-shifted and scaled */
+    LBM_BF16S = 3   /* bfloat16, equilibrium-shifted and scaled */
+};
+
+enum lbm_mode {
+    LBM_COUPLED = 0,  /* f + h + g, velocity from the flow lattice */
+    LBM_FIXED_U = 1   /* f + h only, velocity prescribed by lbm_init_fields */
+};
+
+enum lbm_kernel {
+    LBM_KERNEL_AUTO = 0,   /* library choice (the fused sweep kernel) */
+    LBM_KERNEL_SPLIT = 1,  /* three-kernel chain: moments, normals, collide */
+    LBM_KERNEL_FUSED = 2   /* one fused stream + collide sweep kernel per step */
+};
+
+typedef struct lbm_params {
+    int32_t nx, ny;          /* grid size, each >= 4 */
+    int32_t walls_y;         /* 0: periodic in y; 1: moving walls at y = 0 and y = ny */
+    int32_t mode;            /* enum lbm_mode */
+    int32_t dtype;           /* enum lbm_dtype */
+    int32_t kernel;          /* enum lbm_kernel */
+    int32_t sigma_literal;   /* 1: F_s exactly as Eq. (Fs); 0: scaled by 3W / (2 (phi_a - phi_b)^2)
+                                so that its integral across the interface is sigma * kappa */
+    int32_t reserved;        /* must be 0 */
+    double u_wall;           /* wall speed U_o (x direction): bottom -u_wall, top +u_wall */
+    double W;                /* interface width, Eq. (theta) */
+    double phi_a, phi_b;     /* phase-field bounds, Eq. (CACE) */
+    double M_phi;            /* CACE mobility; M_phi = cs^2 (1/w_kappa - 1/2), App. C */
+    double D_s;              /* surface diffusivity; D_s = cs^2 (1/w_chi - 1/2), Eq. (diffcoeffscalarfield) */
+    double nu_a, nu_b;       /* kinematic viscosities of the two phases (App. D) */
+    double zeta;             /* bulk viscosity; zeta = cs^2 (1/w_zeta - 1/2) (App. D); 1/6 gives w_zeta = 1 */
+    double rho_a, rho_b;     /* densities of the two phases (App. D) */
+    double sigma_o;          /* clean-interface surface tension, Eq. (EOS) */
+    double beta;             /* Gibbs elasticity, Eq. (EOS) */
+    double c_max;            /* maximum concentration Gamma_inf, Eq. (EOS) */
+    double fext_x, fext_y;   /* external body force F_ext */
+} lbm_params;
+
+typedef struct lbm_diag {
+    int64_t step;            /* time steps taken since the last initialisation */
+    double sum_phi, sum_c;   /* FP64 totals of phi and c over the grid */
+    double D, L, B;          /* deformation D = (L - B)/(L + B) (Sec. 4.3, Fig. 8): L = 4 sqrt(l1),
+                                B = 4 sqrt(l2) from the phi-weighted second moments */
+    double xc, yc;           /* phi-weighted centroid (circular mean on periodic axes) */
+    double umax;             /* max |u| */
+    int64_t nonfinite;       /* cells with a non-finite phi, c or u */
+    int64_t sigma_neg;       /* cells where 1 + beta ln(1 - c / c_max) < 0 (Eq. EOS) */
+    int32_t status;          /* LBM_OK, or LBM_ERR_NONFINITE when nonfinite > 0 */
+    int32_t reserved;
+} lbm_diag;
+
+typedef struct lbm_ctx lbm_ctx;
+
+/* Fill *p with the defaults: W 4, phi_a 1, phi_b 0, M_phi 0.1, D_s 0.1,
+ * nu 0.1, zeta 1/6, rho 1, c_max 1, periodic, coupled, FP32, AUTO kernel;
+ * nx = ny = 0 (must be set).  Returns LBM_ERR_INVALID_ARG for p == NULL. */
+int lbm_params_default(lbm_params *p);
+
+/* Validate *p and create a context on the current CUDA device.
+ * stream: a cudaStream_t to run on, or NULL.  Allocates two population
+ * buffers (ping-pong) plus field scratch on the device.
+ * Errors: INVALID_ARG (sizes < 4, NULL, bad enum), RATE (a coefficient <= 0),
+ * UNSUPPORTED (dtype/mode/kernel combination), NOMEM, CUDA. */
+int lbm_create(const lbm_params *p, void *stream, lbm_ctx **out);
+
+/* Release all device and host memory of ctx (NULL is a no-op). */
+void lbm_destroy(lbm_ctx *ctx);
+
+/* Set the state to the discrete equilibria of the given macroscopic fields
+ * (host float64 [ny][nx] arrays; P may be NULL for P = rho cs^2): for each
+ * lattice P^-1 F^-1(u) applied to its equilibrium central moments, with
+ * theta, theta_c and n from the given phi (Sec. 3, App. C, App. D).  In
+ * LBM_FIXED_U mode (ux, uy) is also stored as the prescribed velocity.
+ * Resets the step counter.  Synchronous.  Errors: INVALID_ARG, CUDA. */
+int lbm_init_fields(lbm_ctx *ctx, const double *phi, const double *c, const double *ux,
+                    const double *uy, const double *P);
+
+/* Same with device float64 pointers (e.g. torch tensors on this device).
+ * Asynchronous on the context stream; the inputs must stay valid until the
+ * stream reaches this point. */
+int lbm_init_fields_device(lbm_ctx *ctx, const double *phi, const double *c, const double *ux,
+                           const double *uy, const double *P);
+
+/* Advance nsteps >= 0 time steps: stream, moments, interface geometry,
+ * forces, and the three central-moment collisions.  Asynchronous.  Long runs
+ * replay a captured CUDA graph. */
+int lbm_step(lbm_ctx *ctx, int64_t nsteps);
+
+/* Macroscopic fields of the current state into host float64 [ny][nx]
+ * arrays (any may be NULL): phi = sum f, c = sum h,
+ * u = (sum e g + cs^2 F_t / 2) / (cs^2 rho), P = sum g + Gamma_00 / 2
+ * (App. D update).  In LBM_FIXED_U mode u is the prescribed field and P is 0.
+ * Synchronous. */
+int lbm_get_fields(lbm_ctx *ctx, double *phi, double *c, double *ux, double *uy, double *P);
+
+/* Same into device float64 arrays; asynchronous. */
+int lbm_get_fields_device(lbm_ctx *ctx, double *phi, double *c, double *ux, double *uy,
+                          double *P);
+
+/* Current populations after streaming (the state the next collision reads),
+ * unshifted, as host float64 [9][ny][nx] arrays (any may be NULL; g is
+ * ignored in LBM_FIXED_U mode).  Synchronous. */
+int lbm_get_populations(lbm_ctx *ctx, double *f, double *h, double *g);
+
+/* Replace the state by the given post-streaming populations (host float64
+ * [9][ny][nx]; NULL leaves that lattice unchanged).  Synchronous. */
+int lbm_set_populations(lbm_ctx *ctx, const double *f, const double *h, const double *g);
+
+/* FP64 reductions over the current state into *out (see lbm_diag).
+ * Synchronous.  Returns LBM_OK even when out->status reports non-finite cells. */
+int lbm_diagnostics(lbm_ctx *ctx, lbm_diag *out);
+
+/* Wait for the context stream; report any pending CUDA error. */
+int lbm_synchronize(lbm_ctx *ctx);
+
+/* Steps taken since the last initialisation (-1 for a NULL context). */
+int64_t lbm_get_step(const lbm_ctx *ctx);
+
+/* Kernel variant the context runs (enum lbm_kernel, never AUTO) and the
+ * number of kernel launches one step issues. */
+int lbm_kernel_in_use(const lbm_ctx *ctx);
+int lbm_launches_per_step(const lbm_ctx *ctx);
+
+/* Launch shape of the fused kernel: columns per block (tile_x, a multiple of
+ * 32 in [64, 512]) and rows per block (seg_y >= 4).  0 keeps the current
+ * value.  Errors: INVALID_ARG, UNSUPPORTED (split kernel). */
+int lbm_set_launch_shape(lbm_ctx *ctx, int32_t tile_x, int32_t seg_y);
+int lbm_get_launch_shape(const lbm_ctx *ctx, int32_t *tile_x, int32_t *seg_y);
+
+/* Checkpoint: parameters, step count and raw population buffers to a binary
+ * file, and back (the file must come from a context with equal parameters).
+ * A run continued from a checkpoint is bit-identical to an uninterrupted one.
+ * Errors: IO, INVALID_ARG (parameter mismatch), CUDA. */
+int lbm_save_state(lbm_ctx *ctx, const char *path);
+int lbm_load_state(lbm_ctx *ctx, const char *path);
+
+/* Static description of an error code. */
+const char *lbm_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_H */

@@ -1,0 +1,289 @@
+// Device-side building blocks of the coupled central-moment LBM step
+// (Schupbach & Premnath, arXiv 2504.09024): pull streaming with half-way
+// bounce-back, isotropic stencils, the surface-tension force of Eq. (Fs) with
+// the Langmuir isotherm of Eq. (EOS), and the three central-moment collisions
+// (Sec. 3 Eq. LBE; App. C Eq. LBE_CACE; App. D Eq. centralmomentLBE2fluidflow)
+// written out algebraically for FP32 registers.
+//
+// Storage: post-collision populations, SoA planes [lattice][q][ny][pitch].
+// The flow lattice is stored as g - w_q P0 (P0 = cs2 * reference density) so
+// that FP32 keeps the O(u) information of g; every flow-lattice quantity below
+// is a deviation from the rest state P0 w.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace lbm {
+
+constexpr float CS2 = 1.0f / 3.0f;
+constexpr float EPS_N = 1e-12f;  // |grad phi| below which n = 0
+
+// D2Q9 in the order of the paper's P matrix (App. A).
+__host__ __device__ constexpr int ex(int q) {
+    return (q == 1 || q == 5 || q == 8) ? 1 : ((q == 3 || q == 6 || q == 7) ? -1 : 0);
+}
+__host__ __device__ constexpr int ey(int q) {
+    return (q == 2 || q == 5 || q == 6) ? 1 : ((q == 4 || q == 7 || q == 8) ? -1 : 0);
+}
+__host__ __device__ constexpr int opp(int q) {
+    return q == 0 ? 0 : (q <= 4 ? ((q + 1) % 4 + 1) : ((q - 5 + 2) % 4 + 5));
+}
+__host__ __device__ constexpr float wq(int q) {
+    return q == 0 ? 4.0f / 9.0f : (q <= 4 ? 1.0f / 9.0f : 1.0f / 36.0f);
+}
+
+// Kernel parameters (float copies of lbm_params plus derived rates).
+struct KParams {
+    int nx, ny, pitch, walls;
+    int coupled;
+    int nu_uniform, rho_uniform;
+    int64_t plane;          // pitch * ny
+    float u_wall;
+    float W, phi_a, phi_b, phi_m, inv_dphi;
+    float M_phi, D_s;
+    float w_kappa, w_chi, w_zeta, w_nu;  // w_nu valid when nu_uniform
+    float nu_a, nu_b, rho_a, rho_b, rho_ref;
+    float sigma_o, beta, inv_cmax;
+    float N_sigma;
+    float fext_x, fext_y;
+    float P0;               // rest pressure of the shifted flow storage
+    float four_over_W, eight_over_W;
+};
+
+// ---------------------------------------------------------------------------
+// index helpers
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ int wrap_i(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+
+// Row of the extended field: periodic, or mirrored about the wall planes
+// (row -1-k is row k, row ny+k is row ny-1-k); valid for -2 <= j <= ny+1.
+__device__ __forceinline__ int ext_row(int j, int ny, int walls) {
+    if (!walls) return wrap_i(j, ny);
+    if (j < 0) return -1 - j;
+    if (j >= ny) return 2 * ny - 1 - j;
+    return j;
+}
+// +1 for rows inside or periodic images, -1 for mirrored ghost rows (the
+// y component of the normal field changes sign under the mirror).
+__device__ __forceinline__ float mirror_sign(int j, int ny, int walls) {
+    return (walls && (j < 0 || j >= ny)) ? -1.0f : 1.0f;
+}
+
+// ---------------------------------------------------------------------------
+// streaming (pull) with half-way bounce-back
+// ---------------------------------------------------------------------------
+
+// Gather the 9 post-streaming populations of cell (i, j) of one lattice from
+// the post-collision planes `base` (q-th plane at base + q * plane): a_q(x) =
+// a~_q(x - e_q); a source beyond a wall is replaced by the cell's own opposite
+// slot, which the writer has already bounce-back corrected.
+template <typename T>
+__device__ __forceinline__ void pull9(const T* __restrict__ base, const KParams& p, int i, int j,
+                                      float out[9]) {
+    const int64_t P = p.plane;
+    const int im = wrap_i(i - 1, p.nx), ip = wrap_i(i + 1, p.nx);
+    const int64_t r0 = (int64_t)j * p.pitch;
+    out[0] = (float)base[0 * P + r0 + i];
+    out[1] = (float)base[1 * P + r0 + im];
+    out[3] = (float)base[3 * P + r0 + ip];
+    if (p.walls && j == 0) {
+        out[2] = (float)base[4 * P + r0 + i];
+        out[5] = (float)base[7 * P + r0 + i];
+        out[6] = (float)base[8 * P + r0 + i];
+    } else {
+        const int64_t rm = (int64_t)wrap_i(j - 1, p.ny) * p.pitch;
+        out[2] = (float)base[2 * P + rm + i];
+        out[5] = (float)base[5 * P + rm + im];
+        out[6] = (float)base[6 * P + rm + ip];
+    }
+    if (p.walls && j == p.ny - 1) {
+        out[4] = (float)base[2 * P + r0 + i];
+        out[7] = (float)base[5 * P + r0 + i];
+        out[8] = (float)base[6 * P + r0 + i];
+    } else {
+        const int64_t rp = (int64_t)wrap_i(j + 1, p.ny) * p.pitch;
+        out[4] = (float)base[4 * P + rp + i];
+        out[7] = (float)base[7 * P + rp + ip];
+        out[8] = (float)base[8 * P + rp + im];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// stencils on 3x3 neighbourhoods v[dy+1][dx+1]
+// ---------------------------------------------------------------------------
+
+// Isotropic gradient (1/cs2) sum_q w_q e_q A(x + e_q).
+__device__ __forceinline__ void iso_grad(const float v[3][3], float& gx, float& gy) {
+    gx = (1.0f / 3.0f) * (v[1][2] - v[1][0]) +
+         (1.0f / 12.0f) * ((v[2][2] - v[2][0]) + (v[0][2] - v[0][0]));
+    gy = (1.0f / 3.0f) * (v[2][1] - v[0][1]) +
+         (1.0f / 12.0f) * ((v[2][2] + v[2][0]) - (v[0][2] + v[0][0]));
+}
+
+// Isotropic divergence of a vector field given on the 3x3 neighbourhood.
+__device__ __forceinline__ float iso_div(const float vx[3][3], const float vy[3][3]) {
+    float dxx = (1.0f / 3.0f) * (vx[1][2] - vx[1][0]) +
+                (1.0f / 12.0f) * ((vx[2][2] - vx[2][0]) + (vx[0][2] - vx[0][0]));
+    float dyy = (1.0f / 3.0f) * (vy[2][1] - vy[0][1]) +
+                (1.0f / 12.0f) * ((vy[2][2] + vy[2][0]) - (vy[0][2] + vy[0][0]));
+    return dxx + dyy;
+}
+
+__device__ __forceinline__ void unit_normal(float gx, float gy, float& nx, float& ny, float& mag) {
+    mag = sqrtf(gx * gx + gy * gy);
+    if (mag > EPS_N) {
+        float inv = 1.0f / mag;
+        nx = gx * inv;
+        ny = gy * inv;
+    } else {
+        nx = 0.0f;
+        ny = 0.0f;
+    }
+}
+
+// Langmuir isotherm, Eq. (EOS).
+__device__ __forceinline__ float sigma_of_c(const KParams& p, float c) {
+    return p.sigma_o * (1.0f + p.beta * logf(1.0f - c * p.inv_cmax));
+}
+
+// ---------------------------------------------------------------------------
+// collisions
+// ---------------------------------------------------------------------------
+
+// P^-1 applied to raw moments r = (00,10,01,20,02,11,21,12,22) (App. A).
+__device__ __forceinline__ void raw_to_pops(const float r[9], float out[9]) {
+    out[0] = r[0] - r[3] - r[4] + r[8];
+    out[1] = 0.5f * (r[1] + r[3] - r[7] - r[8]);
+    out[2] = 0.5f * (r[2] + r[4] - r[6] - r[8]);
+    out[3] = 0.5f * (-r[1] + r[3] + r[7] - r[8]);
+    out[4] = 0.5f * (-r[2] + r[4] + r[6] - r[8]);
+    out[5] = 0.25f * (r[5] + r[6] + r[7] + r[8]);
+    out[6] = 0.25f * (-r[5] + r[6] - r[7] + r[8]);
+    out[7] = 0.25f * (r[5] - r[6] - r[7] + r[8]);
+    out[8] = 0.25f * (-r[5] - r[6] + r[7] + r[8]);
+}
+
+// F^-1(u) applied to central moments k (binomial expansion of ((e-u)+u)^m).
+__device__ __forceinline__ void central_to_raw(const float k[9], float ux, float uy, float r[9]) {
+    const float ux2 = ux * ux, uy2 = uy * uy, uxy = ux * uy;
+    r[0] = k[0];
+    r[1] = ux * k[0] + k[1];
+    r[2] = uy * k[0] + k[2];
+    r[3] = ux2 * k[0] + 2.0f * ux * k[1] + k[3];
+    r[4] = uy2 * k[0] + 2.0f * uy * k[2] + k[4];
+    r[5] = uxy * k[0] + uy * k[1] + ux * k[2] + k[5];
+    r[6] = ux2 * uy * k[0] + 2.0f * uxy * k[1] + ux2 * k[2] + uy * k[3] + 2.0f * ux * k[5] + k[6];
+    r[7] = ux * uy2 * k[0] + uy2 * k[1] + 2.0f * uxy * k[2] + ux * k[4] + 2.0f * uy * k[5] + k[7];
+    r[8] = ux2 * uy2 * k[0] + 2.0f * ux * uy2 * k[1] + 2.0f * ux2 * uy * k[2] + uy2 * k[3] +
+           ux2 * k[4] + 4.0f * uxy * k[5] + 2.0f * uy * k[6] + 2.0f * ux * k[7] + k[8];
+}
+
+// Advection-diffusion lattice (f with s = phi, q = M_phi theta n; or h with
+// s = c, q = D_s theta_c n): all central moments are set to their equilibria
+// (s, q, cs2 s, cs2 s, 0, 0, 0, cs4 s) except the first-order ones, which
+// relax at rate w.  In/out: pre-/post-collision populations.
+__device__ __forceinline__ void collide_scalar(float a[9], float s, float qx, float qy, float w,
+                                               float ux, float uy) {
+    const float jx = (a[1] - a[3]) + (a[5] - a[6]) - (a[7] - a[8]);
+    const float jy = (a[2] - a[4]) + (a[5] + a[6]) - (a[7] + a[8]);
+    const float k10 = jx - ux * s, k01 = jy - uy * s;  // central first moments
+    float k[9];
+    k[0] = s;
+    k[1] = k10 + w * (qx - k10);
+    k[2] = k01 + w * (qy - k01);
+    k[3] = CS2 * s;
+    k[4] = CS2 * s;
+    k[5] = 0.0f;
+    k[6] = 0.0f;
+    k[7] = 0.0f;
+    k[8] = CS2 * CS2 * s;
+    float r[9];
+    central_to_raw(k, ux, uy, r);
+    raw_to_pops(r, a);
+}
+
+// Macroscopic inputs of the flow collision at one cell.
+struct FlowMacro {
+    float ux, uy;      // velocity
+    float rho;         // density
+    float dP;          // P - P0 (after the half-source correction)
+    float dPs;         // sum of shifted g = P* - P0
+    float Ftx, Fty;    // total force F_s + F_ext
+    float Fpx, Fpy;    // pressure force -grad psi
+    float w_nu;        // shear relaxation rate
+};
+
+// Flow lattice, Eq. (centralmomentLBE2fluidflow), on shifted populations
+// a = g - w P0.  Central moments of the shift are P0 W(u) with W(u) the
+// central moments of the weights about u; they cancel in eq - moments, so the
+// collision runs on deviations: d_eta^eq = rho cs2 (M(u) - W(u)) + dP W(u).
+__device__ __forceinline__ void collide_flow(float a[9], const FlowMacro& m, float w_zeta) {
+    const float ux = m.ux, uy = m.uy;
+    const float ux2 = ux * ux, uy2 = uy * uy, uxy = ux * uy;
+    // raw moments of the shifted populations that relax at non-unit rates
+    const float jx = (a[1] - a[3]) + (a[5] - a[6]) - (a[7] - a[8]);
+    const float jy = (a[2] - a[4]) + (a[5] + a[6]) - (a[7] + a[8]);
+    const float corner = (a[5] + a[6]) + (a[7] + a[8]);
+    const float r20 = (a[1] + a[3]) + corner;
+    const float r02 = (a[2] + a[4]) + corner;
+    const float r11 = (a[5] - a[6]) + (a[7] - a[8]);
+    const float s0 = m.dPs;
+    // pre-collision central moments (deviation form)
+    const float e20 = r20 - 2.0f * ux * jx + ux2 * s0;
+    const float e02 = r02 - 2.0f * uy * jy + uy2 * s0;
+    const float e11 = r11 - uy * jx - ux * jy + uxy * s0;
+    // equilibria (deviation form); A9 sign reading: first order -psi u
+    const float R = m.rho * CS2, dP = m.dP;
+    const float RmP = R - dP;
+    const float q20 = -R * ux2 + dP * (CS2 + ux2);
+    const float q02 = -R * uy2 + dP * (CS2 + uy2);
+    const float q11 = -RmP * uxy;
+    // source central moments (App. D)
+    const float G = m.Fpx * ux + m.Fpy * uy;
+    const float s10 = CS2 * m.Ftx - ux * G;
+    const float s01 = CS2 * m.Fty - uy * G;
+    const float s20 = 2.0f * CS2 * m.Fpx * ux + (ux2 + CS2) * G;
+    const float s02 = 2.0f * CS2 * m.Fpy * uy + (uy2 + CS2) * G;
+    const float s11 = CS2 * (m.Fpx * uy + m.Fpy * ux) + uxy * G;
+    // relax in the combined basis (B): 2s at w_zeta, 2d and 11 at w_nu, rest at 1
+    const float wn = m.w_nu;
+    const float h2s = e20 + e02, h2d = e20 - e02;
+    const float t2s = h2s + w_zeta * ((q20 + q02) - h2s) + (1.0f - 0.5f * w_zeta) * (s20 + s02);
+    const float t2d = h2d + wn * ((q20 - q02) - h2d) + (1.0f - 0.5f * wn) * (s20 - s02);
+    float k[9];
+    k[0] = dP + 0.5f * G;
+    k[1] = ux * RmP + 0.5f * s10;
+    k[2] = uy * RmP + 0.5f * s01;
+    k[3] = 0.5f * (t2s + t2d);
+    k[4] = 0.5f * (t2s - t2d);
+    k[5] = e11 + wn * (q11 - e11) + (1.0f - 0.5f * wn) * s11;
+    k[6] = RmP * (ux2 + CS2) * uy;
+    k[7] = RmP * (uy2 + CS2) * ux;
+    k[8] = -R * (ux2 * uy2 + CS2 * (ux2 + uy2)) + dP * (ux2 + CS2) * (uy2 + CS2);
+    float r[9];
+    central_to_raw(k, ux, uy, r);
+    raw_to_pops(r, a);
+}
+
+// Moving-wall term added when a flow population is written into a slot that
+// is only read back by the bounce-back of the same cell (App. D set-up,
+// half-way bounce-back): slot q at the bottom row (e_qy = -1) feeds direction
+// opp(q) with u_w = (-u_wall, 0); at the top row (e_qy = +1) u_w = (+u_wall, 0).
+__device__ __forceinline__ void wall_correct_flow(float a[9], const KParams& p, int j, float rho) {
+    if (!p.walls) return;
+    if (j == 0) {
+        // 2 w_opp rho (e_opp . u_w), u_w = -u_wall: opp(4)=2 (0), opp(7)=5 (+1), opp(8)=6 (-1)
+        const float t = 2.0f * (1.0f / 36.0f) * rho * (-p.u_wall);
+        a[7] += t;   // e_5x = +1
+        a[8] -= t;   // e_6x = -1
+    }
+    if (j == p.ny - 1) {
+        const float t = 2.0f * (1.0f / 36.0f) * rho * (p.u_wall);
+        a[5] -= t;   // opp(5) = 7, e_7x = -1
+        a[6] += t;   // opp(6) = 8, e_8x = +1
+    }
+}
+
+}  // namespace lbm

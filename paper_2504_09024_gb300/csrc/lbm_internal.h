@@ -1,0 +1,56 @@
+// Host-side declarations shared by the C-ABI layer and the kernel launchers.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "lbm_device.cuh"
+
+namespace lbm {
+
+// Field scratch planes (float, pitched like the populations).
+enum FieldPlane {
+    FP_PHI = 0, FP_C, FP_DPS, FP_SIG, FP_NX, FP_NY, FP_GM, FP_UX, FP_UY, FP_COUNT
+};
+
+struct DevState {
+    float* pop[2];          // ping-pong population buffers [nlat*9][ny][pitch]
+    float* fields;          // FP_COUNT planes
+    int nlat;               // 2 (fixed velocity) or 3 (coupled)
+};
+
+// Fused-kernel launch shape.
+struct FusedShape {
+    int bx;    // threads per block = interior columns + 4
+    int seg;   // rows per block
+};
+
+// Launchers (all asynchronous on `st`).
+void launch_step_split(const KParams& p, const DevState& s, int src, cudaStream_t st);
+void launch_step_fused(const KParams& p, const DevState& s, int src, const FusedShape& sh,
+                       cudaStream_t st);
+size_t fused_smem_bytes(int bx);
+// Fill the field planes (phi, c, dP*, sigma, n, |grad phi|) of the current state.
+void launch_fields(const KParams& p, const DevState& s, int src, cudaStream_t st);
+// Macroscopic outputs (float64, dense [ny][nx]) of the current state; needs launch_fields first.
+void launch_macro_out(const KParams& p, const DevState& s, int src, double* phi, double* c,
+                      double* ux, double* uy, double* P, cudaStream_t st);
+// Initialisation from float64 fields (dense); writes buffer `dst` (uses the other as scratch).
+void launch_init(const KParams& p, const DevState& s, int dst, const double* phi,
+                 const double* c, const double* ux, const double* uy, const double* P,
+                 cudaStream_t st);
+// Post-streaming populations of buffer src as float64 dense [nlat*9][ny][nx].
+void launch_get_pops(const KParams& p, const DevState& s, int src, double* out, cudaStream_t st);
+// Replace buffer dst by given post-streaming populations (float64 dense [nlat*9][ny][nx]);
+// lattices with a NULL pointer are taken from the current state of dst.
+void launch_set_pops(const KParams& p, const DevState& s, int dst, const double* f,
+                     const double* h, const double* g, cudaStream_t st);
+
+// FP64 reductions: partial sums per block into `partial`, then a fixed-order finish.
+constexpr int DIAG_NSUM = 12;
+int diag_blocks(const KParams& p);
+void launch_diag(const KParams& p, const double* phi, const double* c, const double* ux,
+                 const double* uy, double* partial, int nblocks, double* result,
+                 cudaStream_t st);
+
+}  // namespace lbm

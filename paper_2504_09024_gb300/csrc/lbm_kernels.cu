@@ -1,0 +1,843 @@
+// sm_103a kernels of the coupled central-moment LBM step (arXiv 2504.09024).
+//
+//  * k_fused_sweep  -- the hot path: one launch per time step.  Each block owns
+//    a strip of columns (plus a 2-column halo) and sweeps down a segment of
+//    rows.  Per row it pulls the three lattices, forms phi, c, sigma(c) and
+//    P* into shared-memory row rings, computes the unit normal one row behind,
+//    and collides two rows behind with the curvature, Marangoni and pressure
+//    stencils read from the rings.  Populations are read once per cell (plus
+//    the halo columns and the segment ends) and written once.
+//  * k_fields / k_normals / k_collide -- the same step as a three-kernel chain
+//    with the fields materialised in global memory; used as a cross-check, for
+//    the macroscopic outputs and for initialisation.
+//  * initialisation, population import/export and FP64 reductions.
+#include <cmath>
+
+#include "lbm_internal.h"
+
+namespace lbm {
+
+// ---------------------------------------------------------------------------
+// shared helpers
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ float sum9(const float a[9]) {
+    return ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7])) + a[8];
+}
+
+__device__ __forceinline__ float lerp_phase(const KParams& p, float phi, float va, float vb) {
+    return vb + (phi - p.phi_b) * p.inv_dphi * (va - vb);
+}
+
+__device__ __forceinline__ float rate_from_coeff(float coeff) {
+    return 1.0f / (coeff * 3.0f + 0.5f);
+}
+
+// Deviation-form equilibrium of the flow lattice without source: shifted
+// populations g^eq - w P0 for pressure deviation dP = P - P0.
+__device__ __forceinline__ void eq_flow_shifted(float a[9], float dP, float rho, float ux,
+                                                float uy) {
+    const float ux2 = ux * ux, uy2 = uy * uy, uxy = ux * uy;
+    const float R = rho * CS2, RmP = R - dP;
+    float k[9];
+    k[0] = dP;
+    k[1] = ux * RmP;
+    k[2] = uy * RmP;
+    k[3] = -R * ux2 + dP * (CS2 + ux2);
+    k[4] = -R * uy2 + dP * (CS2 + uy2);
+    k[5] = -RmP * uxy;
+    k[6] = RmP * (ux2 + CS2) * uy;
+    k[7] = RmP * (uy2 + CS2) * ux;
+    k[8] = -R * (ux2 * uy2 + CS2 * (ux2 + uy2)) + dP * (ux2 + CS2) * (uy2 + CS2);
+    float r[9];
+    central_to_raw(k, ux, uy, r);
+    raw_to_pops(r, a);
+}
+
+__device__ __forceinline__ void eq_scalar(float a[9], float s, float qx, float qy, float ux,
+                                          float uy) {
+    float k[9] = {s, qx, qy, CS2 * s, CS2 * s, 0.0f, 0.0f, 0.0f, CS2 * CS2 * s};
+    float r[9];
+    central_to_raw(k, ux, uy, r);
+    raw_to_pops(r, a);
+}
+
+// 3x3 neighbourhood of a field plane on the extended (periodic / mirrored)
+// grid; ysign = -1 flips the sign of mirrored ghost rows (y component of n).
+__device__ __forceinline__ void load3x3(const float* __restrict__ F, const KParams& p, int i, int j,
+                                        float v[3][3], bool odd_under_mirror = false) {
+    const int im = wrap_i(i - 1, p.nx), ip = wrap_i(i + 1, p.nx);
+#pragma unroll
+    for (int dy = -1; dy <= 1; ++dy) {
+        const int jj = j + dy;
+        const int64_t r = (int64_t)ext_row(jj, p.ny, p.walls) * p.pitch;
+        const float s = odd_under_mirror ? mirror_sign(jj, p.ny, p.walls) : 1.0f;
+        v[dy + 1][0] = s * F[r + im];
+        v[dy + 1][1] = s * F[r + i];
+        v[dy + 1][2] = s * F[r + ip];
+    }
+}
+
+// Local values and stencil results one cell's collisions need.
+struct CellGeom {
+    float phi, c, sig, dps;      // zeroth moments, sigma(c), P* - P0
+    float nx, ny, gm;            // unit normal, |grad phi|
+    float kappa;                 // div n
+    float sgx, sgy;              // grad sigma
+    float pgx, pgy;              // grad (P* - P0)
+    float fgx, fgy;              // grad phi (for grad rho)
+};
+
+struct CellOut {
+    float ux, uy, dP;
+};
+
+// The three collisions of one cell at row j (in place on f, h, gg).
+template <bool COUPLED>
+__device__ __forceinline__ CellOut collide_cell(const KParams& p, const CellGeom& g, int j,
+                                                float ux_fixed, float uy_fixed, float f[9],
+                                                float h[9], float gg[9], bool do_collide) {
+    CellOut o;
+    // Eq. (theta) and the theta_c of Eq. (ISS)
+    const float theta = p.four_over_W * (p.phi_a - g.phi) * (g.phi - p.phi_b) * p.inv_dphi;
+    const float theta_c = p.eight_over_W * g.c * (p.phi_m - g.phi) * p.inv_dphi;
+    if (COUPLED) {
+        // surface-tension force, Eq. (Fs)
+        const float g2 = g.gm * g.gm;
+        const float nds = g.nx * g.sgx + g.ny * g.sgy;
+        const float Fsx = p.N_sigma * g2 * (-g.sig * g.kappa * g.nx + (g.sgx - g.nx * nds));
+        const float Fsy = p.N_sigma * g2 * (-g.sig * g.kappa * g.ny + (g.sgy - g.ny * nds));
+        const float Ftx = Fsx + p.fext_x, Fty = Fsy + p.fext_y;
+        const float rho = p.rho_uniform ? p.rho_a : lerp_phase(p, g.phi, p.rho_a, p.rho_b);
+        const float jx = (gg[1] - gg[3]) + (gg[5] - gg[6]) - (gg[7] - gg[8]);
+        const float jy = (gg[2] - gg[4]) + (gg[5] + gg[6]) - (gg[7] + gg[8]);
+        // cs2 rho u = sum e g + cs2 F_t / 2  (App. D)
+        const float inv_rho = 1.0f / rho;
+        o.ux = (3.0f * jx + 0.5f * Ftx) * inv_rho;
+        o.uy = (3.0f * jy + 0.5f * Fty) * inv_rho;
+        // F_p = -grad psi with psi = P* - rho cs2
+        float Fpx = -g.pgx, Fpy = -g.pgy;
+        if (!p.rho_uniform) {
+            const float drho = (p.rho_a - p.rho_b) * p.inv_dphi;
+            Fpx += CS2 * drho * g.fgx;
+            Fpy += CS2 * drho * g.fgy;
+        }
+        const float G = Fpx * o.ux + Fpy * o.uy;
+        o.dP = g.dps + 0.5f * G;  // P = sum g + sigma_00 / 2
+        if (do_collide) {
+            FlowMacro m;
+            m.ux = o.ux;
+            m.uy = o.uy;
+            m.rho = rho;
+            m.dPs = g.dps;
+            m.dP = o.dP;
+            m.Ftx = Ftx;
+            m.Fty = Fty;
+            m.Fpx = Fpx;
+            m.Fpy = Fpy;
+            m.w_nu = p.nu_uniform ? p.w_nu : rate_from_coeff(lerp_phase(p, g.phi, p.nu_a, p.nu_b));
+            collide_flow(gg, m, p.w_zeta);
+            wall_correct_flow(gg, p, j, rho);
+        }
+    } else {
+        o.ux = ux_fixed;
+        o.uy = uy_fixed;
+        o.dP = 0.0f;
+    }
+    if (do_collide) {
+        collide_scalar(f, g.phi, p.M_phi * theta * g.nx, p.M_phi * theta * g.ny, p.w_kappa, o.ux,
+                       o.uy);
+        collide_scalar(h, g.c, p.D_s * theta_c * g.nx, p.D_s * theta_c * g.ny, p.w_chi, o.ux, o.uy);
+    }
+    return o;
+}
+
+__device__ __forceinline__ void store9(float* __restrict__ base, const KParams& p, int64_t idx,
+                                       const float a[9]) {
+#pragma unroll
+    for (int q = 0; q < 9; ++q) base[q * p.plane + idx] = a[q];
+}
+
+// ---------------------------------------------------------------------------
+// three-kernel chain
+// ---------------------------------------------------------------------------
+
+template <bool COUPLED>
+__global__ void k_fields(KParams p, const float* __restrict__ src, float* __restrict__ F) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y;
+    if (i >= p.nx) return;
+    const int64_t idx = (int64_t)j * p.pitch + i;
+    float a[9];
+    pull9(src, p, i, j, a);
+    F[FP_PHI * p.plane + idx] = sum9(a);
+    pull9(src + 9 * p.plane, p, i, j, a);
+    const float c = sum9(a);
+    F[FP_C * p.plane + idx] = c;
+    F[FP_SIG * p.plane + idx] = sigma_of_c(p, c);
+    if (COUPLED) {
+        pull9(src + 18 * p.plane, p, i, j, a);
+        F[FP_DPS * p.plane + idx] = sum9(a);
+    }
+}
+
+__global__ void k_normals(KParams p, float* __restrict__ F) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y;
+    if (i >= p.nx) return;
+    const int64_t idx = (int64_t)j * p.pitch + i;
+    float v[3][3];
+    load3x3(F + FP_PHI * p.plane, p, i, j, v);
+    float gx, gy, nx, ny, gm;
+    iso_grad(v, gx, gy);
+    unit_normal(gx, gy, nx, ny, gm);
+    F[FP_NX * p.plane + idx] = nx;
+    F[FP_NY * p.plane + idx] = ny;
+    F[FP_GM * p.plane + idx] = gm;
+}
+
+template <bool COUPLED>
+__device__ __forceinline__ CellGeom gather_geom(const KParams& p, const float* __restrict__ F, int i,
+                                                int j) {
+    const int64_t idx = (int64_t)j * p.pitch + i;
+    CellGeom g;
+    g.phi = F[FP_PHI * p.plane + idx];
+    g.c = F[FP_C * p.plane + idx];
+    g.nx = F[FP_NX * p.plane + idx];
+    g.ny = F[FP_NY * p.plane + idx];
+    g.gm = F[FP_GM * p.plane + idx];
+    g.sig = F[FP_SIG * p.plane + idx];
+    if (COUPLED) {
+        g.dps = F[FP_DPS * p.plane + idx];
+        float vx[3][3], vy[3][3], v[3][3];
+        load3x3(F + FP_NX * p.plane, p, i, j, vx);
+        load3x3(F + FP_NY * p.plane, p, i, j, vy, true);
+        g.kappa = iso_div(vx, vy);
+        load3x3(F + FP_SIG * p.plane, p, i, j, v);
+        iso_grad(v, g.sgx, g.sgy);
+        load3x3(F + FP_DPS * p.plane, p, i, j, v);
+        iso_grad(v, g.pgx, g.pgy);
+        if (!p.rho_uniform) {
+            load3x3(F + FP_PHI * p.plane, p, i, j, v);
+            iso_grad(v, g.fgx, g.fgy);
+        } else {
+            g.fgx = g.fgy = 0.0f;
+        }
+    } else {
+        g.dps = 0.0f;
+        g.kappa = g.sgx = g.sgy = g.pgx = g.pgy = g.fgx = g.fgy = 0.0f;
+    }
+    return g;
+}
+
+template <bool COUPLED>
+__global__ void k_collide(KParams p, const float* __restrict__ src, float* __restrict__ dst,
+                          const float* __restrict__ F) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y;
+    if (i >= p.nx) return;
+    const int64_t idx = (int64_t)j * p.pitch + i;
+    CellGeom g = gather_geom<COUPLED>(p, F, i, j);
+    float f[9], h[9], gg[9];
+    pull9(src, p, i, j, f);
+    pull9(src + 9 * p.plane, p, i, j, h);
+    float ufx = 0.0f, ufy = 0.0f;
+    if (COUPLED) {
+        pull9(src + 18 * p.plane, p, i, j, gg);
+    } else {
+        ufx = F[FP_UX * p.plane + idx];
+        ufy = F[FP_UY * p.plane + idx];
+    }
+    collide_cell<COUPLED>(p, g, j, ufx, ufy, f, h, gg, true);
+    store9(dst, p, idx, f);
+    store9(dst + 9 * p.plane, p, idx, h);
+    if (COUPLED) store9(dst + 18 * p.plane, p, idx, gg);
+}
+
+template <bool COUPLED>
+__global__ void k_macro_out(KParams p, const float* __restrict__ src, const float* __restrict__ F,
+                            double* __restrict__ ophi, double* __restrict__ oc,
+                            double* __restrict__ oux, double* __restrict__ ouy,
+                            double* __restrict__ oP) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y;
+    if (i >= p.nx) return;
+    const int64_t idx = (int64_t)j * p.pitch + i;
+    const int64_t o = (int64_t)j * p.nx + i;
+    CellGeom g = gather_geom<COUPLED>(p, F, i, j);
+    float gg[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    float ufx = 0.0f, ufy = 0.0f;
+    if (COUPLED) {
+        pull9(src + 18 * p.plane, p, i, j, gg);
+    } else {
+        ufx = F[FP_UX * p.plane + idx];
+        ufy = F[FP_UY * p.plane + idx];
+    }
+    CellOut r = collide_cell<COUPLED>(p, g, j, ufx, ufy, nullptr, nullptr, gg, false);
+    if (ophi) ophi[o] = g.phi;
+    if (oc) oc[o] = g.c;
+    if (oux) oux[o] = r.ux;
+    if (ouy) ouy[o] = r.uy;
+    if (oP) oP[o] = COUPLED ? (double)p.P0 + (double)r.dP : 0.0;
+}
+
+// ---------------------------------------------------------------------------
+// fused sweep kernel
+// ---------------------------------------------------------------------------
+
+constexpr int RING = 5;   // rows kept of phi, c, sigma, P* (current row and four behind)
+constexpr int NRING = 3;  // rows kept of n and |grad phi|
+constexpr int PRING = 3;  // rows of interior populations waiting for their collision
+
+size_t fused_smem_bytes(int bx) {
+    return sizeof(float) * (size_t)bx * (4 * RING + 3 * NRING + 27 * PRING);
+}
+
+// Block = bx threads = bx - 4 interior columns plus two halo columns each side.
+// Rows [y0, y1) are collided; rows y0-2 .. y1+1 are streamed for phi and rows
+// y0-1 .. y1 for c, sigma and P* (ghost rows beyond walls hold the mirrored
+// values, so the stencils there reproduce the mirrored extended field).
+template <bool COUPLED>
+__global__ void __launch_bounds__(128) k_fused_sweep(KParams p, const float* __restrict__ src,
+                                                     float* __restrict__ dst,
+                                                     const float* __restrict__ F, int seg) {
+    extern __shared__ float sm[];
+    const int bx = blockDim.x;
+    const int t = threadIdx.x;
+    float* s_phi = sm;                       // [RING][bx]
+    float* s_c = s_phi + RING * bx;
+    float* s_sig = s_c + RING * bx;
+    float* s_dps = s_sig + RING * bx;
+    float* s_nx = s_dps + RING * bx;         // [NRING][bx]
+    float* s_ny = s_nx + NRING * bx;
+    float* s_gm = s_ny + NRING * bx;
+    float* s_pop = s_gm + NRING * bx;        // [PRING][27][bx]
+
+    const int tx = bx - 4;
+    const int x0 = blockIdx.x * tx;
+    const int xend = min(x0 + tx, p.nx);
+    const int y0 = blockIdx.y * seg;
+    const int y1 = min(y0 + seg, p.ny);
+    const int col = x0 - 2 + t;
+    // role: 3 interior, 2 first halo column, 1 second halo column, 0 idle
+    int role = 0;
+    if (col >= x0 && col < xend) role = 3;
+    else if (col == x0 - 1 || col == xend) role = 2;
+    else if (col == x0 - 2 || col == xend + 1) role = 1;
+    const int i = wrap_i(col, p.nx);
+    const int nl = COUPLED ? 27 : 18;
+
+    float ufx = 0.0f, ufy = 0.0f;
+
+    for (int r = y0 - 2; r <= y1 + 1; ++r) {
+        // A: stream row r and form its moments
+        const int slot = (r + 2 * RING) % RING;
+        if (role > 0) {
+            const int jj = ext_row(r, p.ny, p.walls);
+            float a[9];
+            pull9(src, p, i, jj, a);
+            const float phi = sum9(a);
+            s_phi[slot * bx + t] = phi;
+            const bool interior_row = (r >= y0 && r < y1);
+            float* pp = s_pop + ((r + 3 * PRING) % PRING) * 27 * bx;
+            if (role == 3 && interior_row) {
+#pragma unroll
+                for (int q = 0; q < 9; ++q) pp[q * bx + t] = a[q];
+            }
+            if (role >= 2 && r >= y0 - 1 && r <= y1) {
+                pull9(src + 9 * p.plane, p, i, jj, a);
+                const float c = sum9(a);
+                s_c[slot * bx + t] = c;
+                s_sig[slot * bx + t] = sigma_of_c(p, c);
+                if (role == 3 && interior_row) {
+#pragma unroll
+                    for (int q = 0; q < 9; ++q) pp[(9 + q) * bx + t] = a[q];
+                }
+                if (COUPLED) {
+                    pull9(src + 18 * p.plane, p, i, jj, a);
+                    s_dps[slot * bx + t] = sum9(a);
+                    if (role == 3 && interior_row) {
+#pragma unroll
+                        for (int q = 0; q < 9; ++q) pp[(18 + q) * bx + t] = a[q];
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        // B: normal at row r-1 (needs phi rows r-2 .. r)
+        const int rn = r - 1;
+        if (role >= 2 && rn >= y0 - 1 && rn <= y1) {
+            const int sm1 = (rn - 1 + 2 * RING) % RING, s0 = (rn + 2 * RING) % RING,
+                      sp1 = (rn + 1 + 2 * RING) % RING;
+            float v[3][3];
+            v[0][0] = s_phi[sm1 * bx + t - 1]; v[0][1] = s_phi[sm1 * bx + t]; v[0][2] = s_phi[sm1 * bx + t + 1];
+            v[1][0] = s_phi[s0 * bx + t - 1];  v[1][1] = s_phi[s0 * bx + t];  v[1][2] = s_phi[s0 * bx + t + 1];
+            v[2][0] = s_phi[sp1 * bx + t - 1]; v[2][1] = s_phi[sp1 * bx + t]; v[2][2] = s_phi[sp1 * bx + t + 1];
+            float gx, gy, nx, ny, gm;
+            iso_grad(v, gx, gy);
+            unit_normal(gx, gy, nx, ny, gm);
+            const int ns = (rn + 3 * NRING) % NRING;
+            s_nx[ns * bx + t] = nx;
+            s_ny[ns * bx + t] = ny;
+            s_gm[ns * bx + t] = gm;
+        }
+        __syncthreads();
+        // C: collide row r-2
+        const int jc = r - 2;
+        if (role == 3 && jc >= y0 && jc < y1) {
+            const int cm1 = (jc - 1 + 2 * RING) % RING, c0 = (jc + 2 * RING) % RING,
+                      cp1 = (jc + 1 + 2 * RING) % RING;
+            const int nm1 = (jc - 1 + 3 * NRING) % NRING, n0 = (jc + 3 * NRING) % NRING,
+                      np1 = (jc + 1 + 3 * NRING) % NRING;
+            CellGeom g;
+            g.phi = s_phi[c0 * bx + t];
+            g.c = s_c[c0 * bx + t];
+            g.sig = s_sig[c0 * bx + t];
+            g.nx = s_nx[n0 * bx + t];
+            g.ny = s_ny[n0 * bx + t];
+            g.gm = s_gm[n0 * bx + t];
+            if (COUPLED) {
+                g.dps = s_dps[c0 * bx + t];
+                float vx[3][3], vy[3][3], v[3][3];
+                const int nr[3] = {nm1, n0, np1};
+                const int cr[3] = {cm1, c0, cp1};
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+#pragma unroll
+                    for (int e = 0; e < 3; ++e) {
+                        vx[d][e] = s_nx[nr[d] * bx + t - 1 + e];
+                        vy[d][e] = s_ny[nr[d] * bx + t - 1 + e];
+                    }
+                }
+                g.kappa = iso_div(vx, vy);
+#pragma unroll
+                for (int d = 0; d < 3; ++d)
+#pragma unroll
+                    for (int e = 0; e < 3; ++e) v[d][e] = s_sig[cr[d] * bx + t - 1 + e];
+                iso_grad(v, g.sgx, g.sgy);
+#pragma unroll
+                for (int d = 0; d < 3; ++d)
+#pragma unroll
+                    for (int e = 0; e < 3; ++e) v[d][e] = s_dps[cr[d] * bx + t - 1 + e];
+                iso_grad(v, g.pgx, g.pgy);
+                if (!p.rho_uniform) {
+#pragma unroll
+                    for (int d = 0; d < 3; ++d)
+#pragma unroll
+                        for (int e = 0; e < 3; ++e) v[d][e] = s_phi[cr[d] * bx + t - 1 + e];
+                    iso_grad(v, g.fgx, g.fgy);
+                } else {
+                    g.fgx = g.fgy = 0.0f;
+                }
+            } else {
+                g.dps = 0.0f;
+                g.kappa = g.sgx = g.sgy = g.pgx = g.pgy = g.fgx = g.fgy = 0.0f;
+            }
+            const float* pp = s_pop + ((jc + 3 * PRING) % PRING) * 27 * bx;
+            float f[9], h[9], gg[9];
+#pragma unroll
+            for (int q = 0; q < 9; ++q) {
+                f[q] = pp[q * bx + t];
+                h[q] = pp[(9 + q) * bx + t];
+                gg[q] = COUPLED ? pp[(18 + q) * bx + t] : 0.0f;
+            }
+            const int64_t idx = (int64_t)jc * p.pitch + i;
+            if (!COUPLED) {
+                ufx = F[FP_UX * p.plane + idx];
+                ufy = F[FP_UY * p.plane + idx];
+            }
+            collide_cell<COUPLED>(p, g, jc, ufx, ufy, f, h, gg, true);
+            store9(dst, p, idx, f);
+            store9(dst + 9 * p.plane, p, idx, h);
+            if (COUPLED) store9(dst + 18 * p.plane, p, idx, gg);
+        }
+        (void)nl;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// initialisation and population import / export
+// ---------------------------------------------------------------------------
+
+__global__ void k_init_fields(KParams p, const double* __restrict__ phi,
+                              const double* __restrict__ c, const double* __restrict__ ux,
+                              const double* __restrict__ uy, const double* __restrict__ P,
+                              float* __restrict__ F) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y;
+    if (i >= p.nx) return;
+    const int64_t idx = (int64_t)j * p.pitch + i;
+    const int64_t o = (int64_t)j * p.nx + i;
+    const float fphi = (float)phi[o];
+    const float fc = (float)c[o];
+    F[FP_PHI * p.plane + idx] = fphi;
+    F[FP_C * p.plane + idx] = fc;
+    F[FP_SIG * p.plane + idx] = sigma_of_c(p, fc);
+    F[FP_UX * p.plane + idx] = (float)ux[o];
+    F[FP_UY * p.plane + idx] = (float)uy[o];
+    const double rho = p.rho_uniform ? (double)p.rho_a
+                                     : (double)p.rho_b + ((double)fphi - p.phi_b) * p.inv_dphi *
+                                                             ((double)p.rho_a - p.rho_b);
+    const double Pv = P ? P[o] : rho / 3.0;
+    F[FP_DPS * p.plane + idx] = (float)(Pv - (double)p.P0);
+}
+
+// Equilibrium post-streaming populations into `pre` (dense-pitched [nlat*9]).
+template <bool COUPLED>
+__global__ void k_init_pre(KParams p, const float* __restrict__ F, float* __restrict__ pre) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y;
+    if (i >= p.nx) return;
+    const int64_t idx = (int64_t)j * p.pitch + i;
+    const float phi = F[FP_PHI * p.plane + idx];
+    const float c = F[FP_C * p.plane + idx];
+    const float nx = F[FP_NX * p.plane + idx];
+    const float ny = F[FP_NY * p.plane + idx];
+    const float ux = F[FP_UX * p.plane + idx];
+    const float uy = F[FP_UY * p.plane + idx];
+    const float theta = p.four_over_W * (p.phi_a - phi) * (phi - p.phi_b) * p.inv_dphi;
+    const float theta_c = p.eight_over_W * c * (p.phi_m - phi) * p.inv_dphi;
+    float a[9];
+    eq_scalar(a, phi, p.M_phi * theta * nx, p.M_phi * theta * ny, ux, uy);
+    store9(pre, p, idx, a);
+    eq_scalar(a, c, p.D_s * theta_c * nx, p.D_s * theta_c * ny, ux, uy);
+    store9(pre + 9 * p.plane, p, idx, a);
+    if (COUPLED) {
+        const float rho = p.rho_uniform ? p.rho_a : lerp_phase(p, phi, p.rho_a, p.rho_b);
+        eq_flow_shifted(a, F[FP_DPS * p.plane + idx], rho, ux, uy);
+        store9(pre + 18 * p.plane, p, idx, a);
+    }
+}
+
+// Stored (post-collision, pull-ready) form from post-streaming populations:
+// slot q at y is read by the pull of cell y + e_q, or, when y + e_q lies
+// beyond a wall, by the bounce-back of direction opp(q) at y.
+__global__ void k_unstream(KParams p, int nlat, const float* __restrict__ pre,
+                           float* __restrict__ dst) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y;
+    if (i >= p.nx) return;
+    const int64_t idx = (int64_t)j * p.pitch + i;
+    for (int l = 0; l < nlat; ++l) {
+        const float* pl = pre + (int64_t)l * 9 * p.plane;
+        float* dl = dst + (int64_t)l * 9 * p.plane;
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            const int ti = wrap_i(i + ex(q), p.nx);
+            const int tj = j + ey(q);
+            float v;
+            if (p.walls && (tj < 0 || tj >= p.ny)) {
+                v = pl[opp(q) * p.plane + idx];
+            } else {
+                v = pl[q * p.plane + (int64_t)wrap_i(tj, p.ny) * p.pitch + ti];
+            }
+            dl[q * p.plane + idx] = v;
+        }
+    }
+}
+
+// Post-streaming populations of the stored state (pulled), into a pitched float buffer.
+__global__ void k_pull_pre(KParams p, int nlat, const float* __restrict__ src,
+                           float* __restrict__ pre) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y;
+    if (i >= p.nx) return;
+    const int64_t idx = (int64_t)j * p.pitch + i;
+    for (int l = 0; l < nlat; ++l) {
+        float a[9];
+        pull9(src + (int64_t)l * 9 * p.plane, p, i, j, a);
+        store9(pre + (int64_t)l * 9 * p.plane, p, idx, a);
+    }
+}
+
+// Pitched float pre-form <-> dense float64 host layout, unshifting g.
+__global__ void k_pre_to_f64(KParams p, int nlat, const float* __restrict__ pre,
+                             double* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y;
+    if (i >= p.nx) return;
+    const int64_t idx = (int64_t)j * p.pitch + i;
+    const int64_t n = (int64_t)p.nx * p.ny;
+    const int64_t o = (int64_t)j * p.nx + i;
+    for (int l = 0; l < nlat; ++l)
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            double v = pre[(l * 9 + q) * p.plane + idx];
+            if (l == 2) v += (double)wq(q) * (double)p.P0;
+            out[(l * 9 + q) * n + o] = v;
+        }
+}
+
+__global__ void k_f64_to_pre(KParams p, int lat, const double* __restrict__ in,
+                             float* __restrict__ pre) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y;
+    if (i >= p.nx) return;
+    const int64_t idx = (int64_t)j * p.pitch + i;
+    const int64_t n = (int64_t)p.nx * p.ny;
+    const int64_t o = (int64_t)j * p.nx + i;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+        double v = in[q * n + o];
+        if (lat == 2) v -= (double)wq(q) * (double)p.P0;
+        pre[(lat * 9 + q) * p.plane + idx] = (float)v;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// FP64 reductions (fixed order: per-block partials, one finishing block)
+// ---------------------------------------------------------------------------
+
+constexpr int DIAG_THREADS = 256;
+constexpr double TWO_PI = 6.283185307179586476925286766559;
+
+__device__ __forceinline__ bool finite_cell(double a, double b, double c, double d) {
+    return isfinite(a) && isfinite(b) && isfinite(c) && isfinite(d);
+}
+
+template <int NS>
+__device__ void block_sum(double (&v)[NS], double* partial_out) {
+    __shared__ double red[NS][DIAG_THREADS / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+        double x = v[k];
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if (lane == 0) red[k][w] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < NS; ++k) {
+            double s = 0.0;
+            for (int q = 0; q < DIAG_THREADS / 32; ++q) s += red[k][q];
+            partial_out[k] = s;
+        }
+    }
+}
+
+// Pass 1 sums: phi, c, phi cos/sin(2 pi x / nx), phi cos/sin(2 pi y / ny),
+// phi y, nonfinite count, sigma<0 count, max |u| (as max), spare.
+__global__ void k_diag1(KParams p, const double* __restrict__ phi, const double* __restrict__ c,
+                        const double* __restrict__ ux, const double* __restrict__ uy,
+                        double* __restrict__ partial) {
+    double v[DIAG_NSUM];
+    for (int k = 0; k < DIAG_NSUM; ++k) v[k] = 0.0;
+    double umax = 0.0;
+    const int64_t n = (int64_t)p.nx * p.ny;
+    for (int64_t o = (int64_t)blockIdx.x * DIAG_THREADS + threadIdx.x; o < n;
+         o += (int64_t)gridDim.x * DIAG_THREADS) {
+        const int i = (int)(o % p.nx), j = (int)(o / p.nx);
+        const double f = phi[o], cc = c[o], a = ux[o], b = uy[o];
+        if (!finite_cell(f, cc, a, b)) {
+            v[7] += 1.0;
+            continue;
+        }
+        const double ax = TWO_PI * (i + 0.5) / p.nx, ay = TWO_PI * (j + 0.5) / p.ny;
+        v[0] += f;
+        v[1] += cc;
+        v[2] += f * cos(ax);
+        v[3] += f * sin(ax);
+        v[4] += f * cos(ay);
+        v[5] += f * sin(ay);
+        v[6] += f * (j + 0.5);
+        const double arg = 1.0 - cc * (double)p.inv_cmax;
+        if (arg <= 0.0 || 1.0 + (double)p.beta * log(arg) < 0.0) v[8] += 1.0;
+        umax = fmax(umax, sqrt(a * a + b * b));
+    }
+    for (int o = 16; o > 0; o >>= 1) umax = fmax(umax, __shfl_down_sync(0xffffffffu, umax, o));
+    __shared__ double smax[DIAG_THREADS / 32];
+    if ((threadIdx.x & 31) == 0) smax[threadIdx.x >> 5] = umax;
+    block_sum<DIAG_NSUM>(v, partial + (int64_t)blockIdx.x * DIAG_NSUM);
+    if (threadIdx.x == 0) {
+        double m = 0.0;
+        for (int q = 0; q < DIAG_THREADS / 32; ++q) m = fmax(m, smax[q]);
+        partial[(int64_t)blockIdx.x * DIAG_NSUM + 9] = m;
+    }
+}
+
+// result layout: [0] sum_phi [1] sum_c [2] xc [3] yc [4] nonfinite [5] sigma_neg [6] umax
+//                [7] Ixx [8] Iyy [9] Ixy [10] L [11] B [12] D
+__global__ void k_diag_finish1(KParams p, const double* __restrict__ partial, int nb,
+                               double* __restrict__ res) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double s[DIAG_NSUM];
+    for (int k = 0; k < DIAG_NSUM; ++k) s[k] = 0.0;
+    double m = 0.0;
+    for (int b = 0; b < nb; ++b) {
+        for (int k = 0; k < DIAG_NSUM; ++k)
+            if (k != 9) s[k] += partial[(int64_t)b * DIAG_NSUM + k];
+        m = fmax(m, partial[(int64_t)b * DIAG_NSUM + 9]);
+    }
+    res[0] = s[0];
+    res[1] = s[1];
+    double xc = 0.5 * p.nx, yc = 0.5 * p.ny;
+    if (s[0] != 0.0) {
+        double ax = atan2(s[3], s[2]);
+        if (ax < 0) ax += TWO_PI;
+        xc = ax * p.nx / TWO_PI;
+        if (p.walls) {
+            yc = s[6] / s[0];
+        } else {
+            double ay = atan2(s[5], s[4]);
+            if (ay < 0) ay += TWO_PI;
+            yc = ay * p.ny / TWO_PI;
+        }
+    }
+    res[2] = xc;
+    res[3] = yc;
+    res[4] = s[7];
+    res[5] = s[8];
+    res[6] = m;
+}
+
+__device__ __forceinline__ double min_image(double d, int n, bool periodic) {
+    if (!periodic) return d;
+    while (d >= 0.5 * n) d -= n;
+    while (d < -0.5 * n) d += n;
+    return d;
+}
+
+__global__ void k_diag2(KParams p, const double* __restrict__ phi, const double* __restrict__ c,
+                        const double* __restrict__ ux, const double* __restrict__ uy,
+                        const double* __restrict__ res, double* __restrict__ partial) {
+    double v[3] = {0.0, 0.0, 0.0};
+    const double xc = res[2], yc = res[3];
+    const int64_t n = (int64_t)p.nx * p.ny;
+    for (int64_t o = (int64_t)blockIdx.x * DIAG_THREADS + threadIdx.x; o < n;
+         o += (int64_t)gridDim.x * DIAG_THREADS) {
+        const int i = (int)(o % p.nx), j = (int)(o / p.nx);
+        const double f = phi[o];
+        if (!finite_cell(f, c[o], ux[o], uy[o])) continue;
+        const double dx = min_image(i + 0.5 - xc, p.nx, true);
+        const double dy = min_image(j + 0.5 - yc, p.ny, !p.walls);
+        v[0] += f * dx * dx;
+        v[1] += f * dy * dy;
+        v[2] += f * dx * dy;
+    }
+    block_sum<3>(v, partial + (int64_t)blockIdx.x * DIAG_NSUM);
+}
+
+__global__ void k_diag_finish2(const double* __restrict__ partial, int nb, double* __restrict__ res) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double I[3] = {0.0, 0.0, 0.0};
+    for (int b = 0; b < nb; ++b)
+        for (int k = 0; k < 3; ++k) I[k] += partial[(int64_t)b * DIAG_NSUM + k];
+    const double s0 = res[0];
+    if (s0 != 0.0)
+        for (int k = 0; k < 3; ++k) I[k] /= s0;
+    const double tr = I[0] + I[1], det = I[0] * I[1] - I[2] * I[2];
+    const double disc = sqrt(fmax(0.25 * tr * tr - det, 0.0));
+    const double l1 = 0.5 * tr + disc, l2 = fmax(0.5 * tr - disc, 0.0);
+    const double L = 4.0 * sqrt(l1), B = 4.0 * sqrt(l2);
+    res[7] = I[0];
+    res[8] = I[1];
+    res[9] = I[2];
+    res[10] = L;
+    res[11] = B;
+    res[12] = (L + B) > 0.0 ? (L - B) / (L + B) : 0.0;
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+
+static dim3 row_grid(const KParams& p, int bx) { return dim3((p.nx + bx - 1) / bx, p.ny); }
+
+void launch_fields(const KParams& p, const DevState& s, int src, cudaStream_t st) {
+    const int bx = 128;
+    if (p.coupled)
+        k_fields<true><<<row_grid(p, bx), bx, 0, st>>>(p, s.pop[src], s.fields);
+    else
+        k_fields<false><<<row_grid(p, bx), bx, 0, st>>>(p, s.pop[src], s.fields);
+    k_normals<<<row_grid(p, bx), bx, 0, st>>>(p, s.fields);
+}
+
+void launch_step_split(const KParams& p, const DevState& s, int src, cudaStream_t st) {
+    launch_fields(p, s, src, st);
+    const int bx = 128;
+    if (p.coupled)
+        k_collide<true><<<row_grid(p, bx), bx, 0, st>>>(p, s.pop[src], s.pop[1 - src], s.fields);
+    else
+        k_collide<false><<<row_grid(p, bx), bx, 0, st>>>(p, s.pop[src], s.pop[1 - src], s.fields);
+}
+
+void launch_step_fused(const KParams& p, const DevState& s, int src, const FusedShape& sh,
+                       cudaStream_t st) {
+    const int tx = sh.bx - 4;
+    dim3 grid((p.nx + tx - 1) / tx, (p.ny + sh.seg - 1) / sh.seg);
+    const size_t smem = fused_smem_bytes(sh.bx);
+    if (p.coupled)
+        k_fused_sweep<true><<<grid, sh.bx, smem, st>>>(p, s.pop[src], s.pop[1 - src], s.fields,
+                                                      sh.seg);
+    else
+        k_fused_sweep<false><<<grid, sh.bx, smem, st>>>(p, s.pop[src], s.pop[1 - src], s.fields,
+                                                       sh.seg);
+}
+
+cudaError_t configure_fused_smem() {
+    const int maxb = (int)fused_smem_bytes(128);
+    cudaError_t e = cudaFuncSetAttribute(k_fused_sweep<true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, maxb);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_fused_sweep<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                maxb);
+}
+
+void launch_macro_out(const KParams& p, const DevState& s, int src, double* phi, double* c,
+                      double* ux, double* uy, double* P, cudaStream_t st) {
+    const int bx = 128;
+    if (p.coupled)
+        k_macro_out<true><<<row_grid(p, bx), bx, 0, st>>>(p, s.pop[src], s.fields, phi, c, ux, uy, P);
+    else
+        k_macro_out<false><<<row_grid(p, bx), bx, 0, st>>>(p, s.pop[src], s.fields, phi, c, ux, uy, P);
+}
+
+void launch_init(const KParams& p, const DevState& s, int dst, const double* phi,
+                 const double* c, const double* ux, const double* uy, const double* P,
+                 cudaStream_t st) {
+    const int bx = 128;
+    k_init_fields<<<row_grid(p, bx), bx, 0, st>>>(p, phi, c, ux, uy, P, s.fields);
+    k_normals<<<row_grid(p, bx), bx, 0, st>>>(p, s.fields);
+    float* tmp = s.pop[1 - dst];
+    if (p.coupled)
+        k_init_pre<true><<<row_grid(p, bx), bx, 0, st>>>(p, s.fields, tmp);
+    else
+        k_init_pre<false><<<row_grid(p, bx), bx, 0, st>>>(p, s.fields, tmp);
+    k_unstream<<<row_grid(p, bx), bx, 0, st>>>(p, s.nlat, tmp, s.pop[dst]);
+}
+
+void launch_get_pops(const KParams& p, const DevState& s, int src, double* out, cudaStream_t st) {
+    const int bx = 128;
+    float* tmp = s.pop[1 - src];
+    k_pull_pre<<<row_grid(p, bx), bx, 0, st>>>(p, s.nlat, s.pop[src], tmp);
+    k_pre_to_f64<<<row_grid(p, bx), bx, 0, st>>>(p, s.nlat, tmp, out);
+}
+
+void launch_set_pops(const KParams& p, const DevState& s, int dst, const double* f,
+                     const double* h, const double* g, cudaStream_t st) {
+    const int bx = 128;
+    float* tmp = s.pop[1 - dst];
+    k_pull_pre<<<row_grid(p, bx), bx, 0, st>>>(p, s.nlat, s.pop[dst], tmp);
+    const double* in[3] = {f, h, g};
+    for (int l = 0; l < s.nlat; ++l)
+        if (in[l]) k_f64_to_pre<<<row_grid(p, bx), bx, 0, st>>>(p, l, in[l], tmp);
+    k_unstream<<<row_grid(p, bx), bx, 0, st>>>(p, s.nlat, tmp, s.pop[dst]);
+}
+
+int diag_blocks(const KParams& p) {
+    const int64_t n = (int64_t)p.nx * p.ny;
+    int64_t b = (n + DIAG_THREADS * 8 - 1) / (DIAG_THREADS * 8);
+    if (b < 1) b = 1;
+    if (b > 1024) b = 1024;
+    return (int)b;
+}
+
+void launch_diag(const KParams& p, const double* phi, const double* c, const double* ux,
+                 const double* uy, double* partial, int nb, double* result, cudaStream_t st) {
+    k_diag1<<<nb, DIAG_THREADS, 0, st>>>(p, phi, c, ux, uy, partial);
+    k_diag_finish1<<<1, 32, 0, st>>>(p, partial, nb, result);
+    k_diag2<<<nb, DIAG_THREADS, 0, st>>>(p, phi, c, ux, uy, result, partial);
+    k_diag_finish2<<<1, 32, 0, st>>>(partial, nb, result);
+}
+
+}  // namespace lbm

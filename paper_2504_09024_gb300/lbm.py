@@ -1,0 +1,316 @@
+"""Thin ctypes binding of liblbm.so (include/lbm.h).
+
+Functions carry the C names and only marshal arguments: every step of the
+method runs in the library's CUDA kernels.  There is no CPU fallback; if the
+library is missing or fails to load, the first call raises.
+
+Field arrays are float64 [ny][nx]; population arrays float64 [9][ny][nx].
+Host arguments may be numpy arrays (any float64 C-contiguous buffer) or
+pinned torch CPU tensors; ``*_device`` functions take CUDA torch tensors (or
+raw integer device pointers).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Optional
+
+import numpy as np
+
+from . import build as _build
+
+LBM_OK = 0
+LBM_ERR_INVALID_ARG = -1
+LBM_ERR_RATE = -2
+LBM_ERR_SIGMA_NEG = -3
+LBM_ERR_CUDA = -4
+LBM_ERR_NONFINITE = -5
+LBM_ERR_TIMEOUT = -6
+LBM_ERR_UNSUPPORTED = -7
+LBM_ERR_IO = -8
+LBM_ERR_NOMEM = -9
+
+LBM_F32, LBM_F16S, LBM_BF16S = 1, 2, 3
+LBM_COUPLED, LBM_FIXED_U = 0, 1
+LBM_KERNEL_AUTO, LBM_KERNEL_SPLIT, LBM_KERNEL_FUSED = 0, 1, 2
+
+
+class lbm_params(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("walls_y", ctypes.c_int32),
+        ("mode", ctypes.c_int32), ("dtype", ctypes.c_int32), ("kernel", ctypes.c_int32),
+        ("sigma_literal", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("u_wall", ctypes.c_double), ("W", ctypes.c_double), ("phi_a", ctypes.c_double),
+        ("phi_b", ctypes.c_double), ("M_phi", ctypes.c_double), ("D_s", ctypes.c_double),
+        ("nu_a", ctypes.c_double), ("nu_b", ctypes.c_double), ("zeta", ctypes.c_double),
+        ("rho_a", ctypes.c_double), ("rho_b", ctypes.c_double), ("sigma_o", ctypes.c_double),
+        ("beta", ctypes.c_double), ("c_max", ctypes.c_double), ("fext_x", ctypes.c_double),
+        ("fext_y", ctypes.c_double),
+    ]
+
+
+class lbm_diag(ctypes.Structure):
+    _fields_ = [
+        ("step", ctypes.c_int64), ("sum_phi", ctypes.c_double), ("sum_c", ctypes.c_double),
+        ("D", ctypes.c_double), ("L", ctypes.c_double), ("B", ctypes.c_double),
+        ("xc", ctypes.c_double), ("yc", ctypes.c_double), ("umax", ctypes.c_double),
+        ("nonfinite", ctypes.c_int64), ("sigma_neg", ctypes.c_int64),
+        ("status", ctypes.c_int32), ("reserved", ctypes.c_int32),
+    ]
+
+
+# Every symbol include/lbm.h declares, with (restype, argtypes).
+_VP = ctypes.c_void_p
+_DP = ctypes.c_void_p  # double* passed as an address
+SIGNATURES = {
+    "lbm_params_default": (ctypes.c_int, [ctypes.POINTER(lbm_params)]),
+    "lbm_create": (ctypes.c_int, [ctypes.POINTER(lbm_params), _VP, ctypes.POINTER(_VP)]),
+    "lbm_destroy": (None, [_VP]),
+    "lbm_init_fields": (ctypes.c_int, [_VP, _DP, _DP, _DP, _DP, _DP]),
+    "lbm_init_fields_device": (ctypes.c_int, [_VP, _DP, _DP, _DP, _DP, _DP]),
+    "lbm_step": (ctypes.c_int, [_VP, ctypes.c_int64]),
+    "lbm_get_fields": (ctypes.c_int, [_VP, _DP, _DP, _DP, _DP, _DP]),
+    "lbm_get_fields_device": (ctypes.c_int, [_VP, _DP, _DP, _DP, _DP, _DP]),
+    "lbm_get_populations": (ctypes.c_int, [_VP, _DP, _DP, _DP]),
+    "lbm_set_populations": (ctypes.c_int, [_VP, _DP, _DP, _DP]),
+    "lbm_diagnostics": (ctypes.c_int, [_VP, ctypes.POINTER(lbm_diag)]),
+    "lbm_synchronize": (ctypes.c_int, [_VP]),
+    "lbm_get_step": (ctypes.c_int64, [_VP]),
+    "lbm_kernel_in_use": (ctypes.c_int, [_VP]),
+    "lbm_launches_per_step": (ctypes.c_int, [_VP]),
+    "lbm_set_launch_shape": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32]),
+    "lbm_get_launch_shape": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int32),
+                                            ctypes.POINTER(ctypes.c_int32)]),
+    "lbm_save_state": (ctypes.c_int, [_VP, ctypes.c_char_p]),
+    "lbm_load_state": (ctypes.c_int, [_VP, ctypes.c_char_p]),
+    "lbm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+}
+
+_lib = None
+_lock = threading.Lock()
+
+
+def library_path() -> str:
+    return _build.SO
+
+
+def load(build_if_missing: bool = True):
+    """Load liblbm.so (building it first if allowed and missing)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.SO
+            if not os.path.exists(path):
+                if not build_if_missing:
+                    raise RuntimeError(f"liblbm.so not built ({path}); run __graft_entry__.build()")
+                _build.build()
+            L = ctypes.CDLL(path)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+class LBMError(RuntimeError):
+    def __init__(self, code, where=""):
+        self.code = code
+        msg = load().lbm_strerror(code).decode()
+        super().__init__(f"{where}: {msg} ({code})")
+
+
+def _check(code, where):
+    if code != LBM_OK:
+        raise LBMError(code, where)
+    return code
+
+
+def _addr(a, dtype=np.float64):
+    """Address of a host or device buffer (numpy array, torch tensor, int or None)."""
+    if a is None:
+        return None
+    if isinstance(a, int):
+        return a
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    if not (isinstance(a, np.ndarray) and a.dtype == dtype and a.flags.c_contiguous):
+        raise TypeError("expected a C-contiguous float64 numpy array")
+    return a.ctypes.data
+
+
+# --- C-named wrappers ------------------------------------------------------
+
+def lbm_params_default() -> lbm_params:
+    p = lbm_params()
+    _check(load().lbm_params_default(ctypes.byref(p)), "lbm_params_default")
+    return p
+
+
+def lbm_create(p: lbm_params, stream: Optional[int] = None) -> int:
+    h = _VP()
+    _check(load().lbm_create(ctypes.byref(p), stream, ctypes.byref(h)), "lbm_create")
+    return h.value
+
+
+def lbm_destroy(ctx: int) -> None:
+    load().lbm_destroy(ctx)
+
+
+def lbm_init_fields(ctx, phi, c, ux, uy, P=None):
+    _check(load().lbm_init_fields(ctx, _addr(phi), _addr(c), _addr(ux), _addr(uy), _addr(P)),
+           "lbm_init_fields")
+
+
+def lbm_init_fields_device(ctx, phi, c, ux, uy, P=None):
+    _check(load().lbm_init_fields_device(ctx, _addr(phi), _addr(c), _addr(ux), _addr(uy),
+                                         _addr(P)), "lbm_init_fields_device")
+
+
+def lbm_step(ctx, nsteps: int):
+    _check(load().lbm_step(ctx, int(nsteps)), "lbm_step")
+
+
+def lbm_get_fields(ctx, phi=None, c=None, ux=None, uy=None, P=None):
+    _check(load().lbm_get_fields(ctx, _addr(phi), _addr(c), _addr(ux), _addr(uy), _addr(P)),
+           "lbm_get_fields")
+
+
+def lbm_get_fields_device(ctx, phi=None, c=None, ux=None, uy=None, P=None):
+    _check(load().lbm_get_fields_device(ctx, _addr(phi), _addr(c), _addr(ux), _addr(uy),
+                                        _addr(P)), "lbm_get_fields_device")
+
+
+def lbm_get_populations(ctx, f=None, h=None, g=None):
+    _check(load().lbm_get_populations(ctx, _addr(f), _addr(h), _addr(g)), "lbm_get_populations")
+
+
+def lbm_set_populations(ctx, f=None, h=None, g=None):
+    _check(load().lbm_set_populations(ctx, _addr(f), _addr(h), _addr(g)), "lbm_set_populations")
+
+
+def lbm_diagnostics(ctx) -> dict:
+    d = lbm_diag()
+    _check(load().lbm_diagnostics(ctx, ctypes.byref(d)), "lbm_diagnostics")
+    return {name: getattr(d, name) for name, _ in lbm_diag._fields_ if name != "reserved"}
+
+
+def lbm_synchronize(ctx):
+    _check(load().lbm_synchronize(ctx), "lbm_synchronize")
+
+
+def lbm_get_step(ctx) -> int:
+    return int(load().lbm_get_step(ctx))
+
+
+def lbm_kernel_in_use(ctx) -> int:
+    return int(load().lbm_kernel_in_use(ctx))
+
+
+def lbm_launches_per_step(ctx) -> int:
+    return int(load().lbm_launches_per_step(ctx))
+
+
+def lbm_set_launch_shape(ctx, tile_x=0, seg_y=0):
+    _check(load().lbm_set_launch_shape(ctx, int(tile_x), int(seg_y)), "lbm_set_launch_shape")
+
+
+def lbm_get_launch_shape(ctx):
+    a, b = ctypes.c_int32(), ctypes.c_int32()
+    _check(load().lbm_get_launch_shape(ctx, ctypes.byref(a), ctypes.byref(b)),
+           "lbm_get_launch_shape")
+    return a.value, b.value
+
+
+def lbm_save_state(ctx, path: str):
+    _check(load().lbm_save_state(ctx, path.encode()), "lbm_save_state")
+
+
+def lbm_load_state(ctx, path: str):
+    _check(load().lbm_load_state(ctx, path.encode()), "lbm_load_state")
+
+
+def lbm_strerror(code: int) -> str:
+    return load().lbm_strerror(code).decode()
+
+
+# --- convenience object ----------------------------------------------------
+
+def params_from(phys, dtype=LBM_F32, kernel=LBM_KERNEL_AUTO) -> lbm_params:
+    """lbm_params from a workloads.Physics (or any object/dict with the fields)."""
+    d = phys.as_dict() if hasattr(phys, "as_dict") else dict(phys)
+    p = lbm_params_default()
+    for name, _ in lbm_params._fields_:
+        if name in d:
+            setattr(p, name, d[name])
+    p.dtype = dtype
+    p.kernel = kernel
+    return p
+
+
+class Sim:
+    """A context plus numpy-facing helpers (all work runs in liblbm.so)."""
+
+    def __init__(self, phys, dtype=LBM_F32, kernel=LBM_KERNEL_AUTO, stream=None):
+        self.nx, self.ny = int(phys.nx), int(phys.ny)
+        self.mode = int(getattr(phys, "mode", 0))
+        self.params = params_from(phys, dtype, kernel)
+        self.ctx = lbm_create(self.params, stream)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            lbm_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init(self, phi, c, ux, uy, P=None):
+        a = [None if v is None else np.ascontiguousarray(v, dtype=np.float64)
+             for v in (phi, c, ux, uy, P)]
+        lbm_init_fields(self.ctx, *a)
+
+    def step(self, n=1):
+        lbm_step(self.ctx, n)
+
+    def sync(self):
+        lbm_synchronize(self.ctx)
+
+    @property
+    def t(self):
+        return lbm_get_step(self.ctx)
+
+    def fields(self):
+        out = [np.zeros((self.ny, self.nx)) for _ in range(5)]
+        lbm_get_fields(self.ctx, *out)
+        return dict(zip(("phi", "c", "ux", "uy", "P"), out))
+
+    def pops(self):
+        n = 2 if self.mode == LBM_FIXED_U else 3
+        out = [np.zeros((9, self.ny, self.nx)) for _ in range(n)]
+        lbm_get_populations(self.ctx, *out)
+        return dict(zip(("f", "h", "g"), out))
+
+    def set_pops(self, f=None, h=None, g=None):
+        a = [None if v is None else np.ascontiguousarray(v, dtype=np.float64) for v in (f, h, g)]
+        lbm_set_populations(self.ctx, *a)
+
+    def diagnostics(self):
+        return lbm_diagnostics(self.ctx)
+
+    @property
+    def kernel(self):
+        return lbm_kernel_in_use(self.ctx)
+
+    def set_launch_shape(self, tile_x=0, seg_y=0):
+        lbm_set_launch_shape(self.ctx, tile_x, seg_y)
+
+    def save(self, path):
+        lbm_save_state(self.ctx, path)
+
+    def load(self, path):
+        lbm_load_state(self.ctx, path)

@@ -101,7 +101,7 @@ def drop_fields(nx, ny, R, W, xc=None, yc=None, phi_a=1.0, phi_b=0.0,
     phi = phi_m + phi_o * np.tanh(2.0 * zeta / W)
     theta = np.arctan2(dy, dx)
     chat = c_of_theta(theta) if c_of_theta is not None else np.full_like(r, c0)
-    c = chat / np.cosh(2.0 * zeta / W) ** 2
+    c = chat / np.cosh(np.clip(2.0 * zeta / W, -300.0, 300.0)) ** 2
     return phi, c
 
 
@@ -112,7 +112,7 @@ def flat_band_fields(nx, ny, y1, y2, W, phi_a=1.0, phi_b=0.0, c0=0.0):
     phi_m = 0.5 * (phi_a + phi_b)
     phi_o = 0.5 * (phi_a - phi_b)
     phi = phi_m + phi_o * np.tanh(2.0 * zeta / W)
-    c = c0 / np.cosh(2.0 * zeta / W) ** 2
+    c = c0 / np.cosh(np.clip(2.0 * zeta / W, -300.0, 300.0)) ** 2
     return phi, c
 
 

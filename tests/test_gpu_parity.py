@@ -1,0 +1,227 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerance: relative L2 error <= 1e-5 for phi, c (Gamma) and u after 1000
+steps with FP32 populations, the bound the method's FP32 target states.  A
+one-step comparison at the full 2048x1024 size starts both sides from the same
+(GPU) state and checks every cell.
+"""
+import os
+import tempfile
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2504_09024_gb300 import lbm, workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+KERNELS = [lbm.LBM_KERNEL_FUSED, lbm.LBM_KERNEL_SPLIT]
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def umag(F):
+    return np.hypot(F["ux"], F["uy"])
+
+
+def run_gpu(case, kernel, steps=None):
+    s = lbm.Sim(case.phys, kernel=kernel)
+    s.init(case.phi, case.c, case.ux, case.uy, case.P)
+    s.step(case.steps if steps is None else steps)
+    return s
+
+
+_oracle_cache = {}
+
+
+def oracle_fields(case, steps):
+    key = (case.name, case.phys.nx, case.phys.ny, steps)
+    if key not in _oracle_cache:
+        _oracle_cache[key] = oracle.run_case(case, steps=steps).fields()
+    return _oracle_cache[key]
+
+
+def check_fields(got, ref, with_u=True, tol=TOL):
+    errs = {k: rel(got[k], ref[k]) for k in ("phi", "c")}
+    if with_u:
+        errs["u"] = rel(umag(got), umag(ref))
+    for k, e in errs.items():
+        assert e <= tol, (k, e, errs)
+    return errs
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_static_drop_cos_mode_1000_steps(kernel):
+    case = W.static_drop_cos_mode()
+    got = run_gpu(case, kernel, 1000).fields()
+    check_fields(got, oracle_fields(case, 1000), with_u=False)
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_lively_shear_drop_1000_steps(kernel):
+    case = W.lively_shear_drop()
+    got = run_gpu(case, kernel, 1000).fields()
+    errs = check_fields(got, oracle_fields(case, 1000))
+    ref = oracle_fields(case, 1000)
+    assert rel(got["P"], ref["P"]) < 1e-6, errs
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_shear_drop_512x256_1000_steps(kernel):
+    case = W.shear_drop_512x256(steps=1000)
+    got = run_gpu(case, kernel).fields()
+    check_fields(got, oracle_fields(case, 1000))
+
+
+def test_periodic_vortex_coupled():
+    nx, ny = 70, 52
+    phys = W.Physics(nx=nx, ny=ny, walls_y=0, mode=0, M_phi=0.03, D_s=0.02,
+                     nu_a=0.1, nu_b=0.1, sigma_o=2e-3, beta=0.3)
+    phi, c = W.drop_fields(nx, ny, 12.0, 4.0, c_of_theta=lambda t: 0.3 + 0.1 * np.cos(t))
+    X, Y = W.cell_centres(nx, ny)
+    ux = 0.02 * np.sin(2 * np.pi * X / nx) * np.cos(2 * np.pi * Y / ny)
+    uy = -0.02 * (ny / nx) * np.cos(2 * np.pi * X / nx) * np.sin(2 * np.pi * Y / ny)
+    case = W.Case("vortex", phys, phi, c, ux, uy, None, 400)
+    ref = oracle_fields(case, 400)
+    for kernel in KERNELS:
+        check_fields(run_gpu(case, kernel).fields(), ref)
+
+
+@pytest.mark.parametrize("shape", [(4, 4), (5, 7), (125, 9), (129, 33), (64, 5)])
+@pytest.mark.parametrize("walls", [0, 1])
+def test_small_and_ragged_grids(shape, walls):
+    nx, ny = shape
+    phys = W.Physics(nx=nx, ny=ny, walls_y=walls, mode=0, u_wall=0.01 * walls, M_phi=0.05,
+                     D_s=0.05, nu_a=0.1, nu_b=0.1, sigma_o=3e-3, beta=0.2)
+    R = max(1.5, min(nx, ny) / 3.0)
+    phi, c = W.drop_fields(nx, ny, R, 2.0, c_of_theta=lambda t: 0.2 + 0.1 * np.cos(t))
+    ux, uy = (W.shear_profile(nx, ny, 0.01) if walls else (np.zeros_like(phi), np.zeros_like(phi)))
+    case = W.Case(f"small{nx}x{ny}w{walls}", phys, phi, c, ux, uy, None, 60)
+    ref = oracle_fields(case, 60)
+    for kernel in KERNELS:
+        got = run_gpu(case, kernel).fields()
+        for k in ("phi", "c", "ux", "uy", "P"):
+            scale = max(np.abs(ref[k]).max(), 1e-12)
+            assert np.abs(got[k] - ref[k]).max() <= 1e-5 * scale + 1e-9, (kernel, k)
+
+
+def test_init_populations_match_oracle():
+    case = W.lively_shear_drop()
+    g = run_gpu(case, lbm.LBM_KERNEL_FUSED, 0).pops()
+    o = oracle.run_case(case, steps=0).pops()
+    for k in ("f", "h", "g"):
+        assert np.abs(g[k] - o[k]).max() < 2e-7, k
+
+
+def test_set_get_populations_roundtrip():
+    case = W.lively_shear_drop()
+    o = oracle.run_case(case, steps=50).pops()
+    s = lbm.Sim(case.phys)
+    s.init(case.phi, case.c, case.ux, case.uy)
+    s.set_pops(**o)
+    back = s.pops()
+    for k in ("f", "h", "g"):
+        assert np.abs(back[k] - o[k]).max() < 1e-7, k
+
+
+def test_fused_matches_split():
+    case = W.lively_shear_drop()
+    a = run_gpu(case, lbm.LBM_KERNEL_FUSED, 300).pops()
+    b = run_gpu(case, lbm.LBM_KERNEL_SPLIT, 300).pops()
+    for k in ("f", "h", "g"):
+        assert np.abs(a[k] - b[k]).max() < 1e-6, k
+
+
+def test_one_step_full_size_2048x1024():
+    """Bench workload size: advance the GPU, hand its state to the oracle,
+    take one more step on both and compare every cell."""
+    case = W.shear_drop_2048x1024(Ca=0.1, steps=40)
+    s = run_gpu(case, lbm.LBM_KERNEL_FUSED)
+    pre = s.pops()
+    orc = oracle.Sim(case.phys)
+    orc.set_pops(**pre)
+    orc.step(1)
+    ref = orc.fields()
+    ref_pops = orc.pops()
+    s.step(1)
+    got = s.fields()
+    got_pops = s.pops()
+    check_fields(got, ref)
+    for k in ("f", "h", "g"):
+        assert np.abs(got_pops[k] - ref_pops[k]).max() < 2e-7, k
+    orc.close()
+
+
+def test_diagnostics_match_oracle():
+    case = W.lively_shear_drop()
+    s = run_gpu(case, lbm.LBM_KERNEL_FUSED, 500)
+    d = s.diagnostics()
+    o = oracle.run_case(case, steps=500).diagnostics()
+    assert d["step"] == 500 and d["nonfinite"] == 0 and d["status"] == 0
+    for k in ("sum_phi", "sum_c", "xc", "yc", "L", "B"):
+        assert abs(d[k] - o[k]) <= 1e-5 * abs(o[k]) + 1e-9, (k, d[k], o[k])
+    assert abs(d["D"] - o["D"]) < 1e-4
+    assert abs(d["umax"] - o["umax"]) < 1e-5 * o["umax"]
+
+
+def test_conservation_fp32():
+    case = W.lively_shear_drop()
+    s = lbm.Sim(case.phys)
+    s.init(case.phi, case.c, case.ux, case.uy)
+    d0 = s.diagnostics()
+    s.step(2000)
+    d1 = s.diagnostics()
+    assert abs(d1["sum_phi"] - d0["sum_phi"]) < 1e-5 * d0["sum_phi"]
+    assert abs(d1["sum_c"] - d0["sum_c"]) < 1e-5 * d0["sum_c"]
+
+
+def test_checkpoint_resume_bit_exact():
+    case = W.lively_shear_drop()
+    a = run_gpu(case, lbm.LBM_KERNEL_FUSED, 200).pops()
+    s = run_gpu(case, lbm.LBM_KERNEL_FUSED, 100)
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, "ck.bin")
+        s.save(path)
+        s.close()
+        t = lbm.Sim(case.phys)
+        t.load(path)
+        assert t.t == 100
+        t.step(100)
+        b = t.pops()
+    for k in ("f", "h", "g"):
+        assert np.array_equal(a[k], b[k]), k
+
+
+def test_graph_replay_matches_single_launches():
+    case = W.lively_shear_drop()
+    a = run_gpu(case, lbm.LBM_KERNEL_FUSED, 70).pops()  # two graphs + 6 single steps
+    s = lbm.Sim(case.phys)
+    s.init(case.phi, case.c, case.ux, case.uy)
+    for _ in range(70):
+        s.step(1)
+    b = s.pops()
+    for k in ("f", "h", "g"):
+        assert np.array_equal(a[k], b[k]), k
+
+
+def test_sigma_negative_rejected():
+    case = W.lively_shear_drop()
+    case.phys.beta = 2.0
+    s = lbm.Sim(case.phys)
+    with pytest.raises(lbm.LBMError) as e:
+        s.init(case.phi, case.c * 3.0, case.ux, case.uy)
+    assert e.value.code == lbm.LBM_ERR_SIGMA_NEG
+
+
+def test_nonfinite_reported():
+    case = W.lively_shear_drop()
+    phi = case.phi.copy()
+    phi[10, 10] = np.nan
+    s = lbm.Sim(case.phys)
+    s.init(phi, case.c, case.ux, case.uy)
+    d = s.diagnostics()
+    assert d["nonfinite"] > 0 and d["status"] == lbm.LBM_ERR_NONFINITE
