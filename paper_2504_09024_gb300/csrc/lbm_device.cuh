@@ -5,10 +5,15 @@
 // (Sec. 3 Eq. LBE; App. C Eq. LBE_CACE; App. D Eq. centralmomentLBE2fluidflow)
 // written out algebraically for FP32 registers.
 //
-// Storage: post-collision populations, SoA planes [lattice][q][ny][pitch].
-// The flow lattice is stored as g - w_q P0 (P0 = cs2 * reference density) so
-// that FP32 keeps the O(u) information of g; every flow-lattice quantity below
-// is a deviation from the rest state P0 w.
+// Storage: post-collision state, SoA planes [lattice][q][ny][pitch], read by a
+// pull.  Both advection-diffusion lattices (f, h) are kept in deviation form:
+// plane 0 holds the post-collision zeroth moment S (= phi or c) and planes
+// 1..8 hold d_q = a~_q - w_q S (the rest deviation is -sum d_q).  S is written
+// with unbiased stochastic rounding: a slowly evolving interface changes S by
+// less than half an FP32 ulp per step, which round-to-nearest would drop every
+// step.  The flow lattice is stored as g - w_q P0 (P0 = cs2 * reference
+// density) so that FP32 keeps the O(u) information of g; every flow-lattice
+// quantity below is a deviation from the rest state P0 w.
 #pragma once
 
 #include <cstdint>
@@ -110,6 +115,139 @@ __device__ __forceinline__ void pull9(const T* __restrict__ base, const KParams&
     }
 }
 
+// Zeroth and first moments of the post-streaming populations of a lattice in
+// deviation form (plane 0: S, planes 1..8: d_q):
+//   a_q(x) = w_q S(x - e_q) + d_q(x - e_q)           (q >= 1, pulled)
+//   a_0(x) = w_0 S(x) - sum_{q>=1} d_q(x)            (rest, own cell)
+// so that  sum_q a_q(x) = S(x) + inc  with the small increment
+//   inc = sum_{q>=1} [w_q (S(x-e_q) - S(x)) + d_q(x-e_q)] - sum_{q>=1} d_q(x)
+// and  sum_q e_q a_q(x) = sum_{q>=1} e_q [w_q (S(x-e_q) - S(x)) + d_q(x-e_q)].
+// A source beyond a wall is the cell's own opposite slot (bounce-back).
+struct ScalarMoments {
+    float s0;    // S(x)
+    float inc;   // zeroth moment = s0 + inc
+    float jx, jy;
+};
+
+template <typename T>
+__device__ __forceinline__ ScalarMoments pull_scalar(const T* __restrict__ base, const KParams& p,
+                                                     int i, int j) {
+    const int64_t P = p.plane;
+    const int im = wrap_i(i - 1, p.nx), ip = wrap_i(i + 1, p.nx);
+    const int64_t r0 = (int64_t)j * p.pitch;
+    const bool bot = p.walls && j == 0, top = p.walls && j == p.ny - 1;
+    const float S0 = (float)base[r0 + i];
+    float o[9];
+#pragma unroll
+    for (int q = 1; q < 9; ++q) o[q] = (float)base[q * P + r0 + i];
+    const float w1 = 1.0f / 9.0f, w5 = 1.0f / 36.0f;
+    float t[9];
+    t[1] = w1 * ((float)base[r0 + im] - S0) + (float)base[1 * P + r0 + im];
+    t[3] = w1 * ((float)base[r0 + ip] - S0) + (float)base[3 * P + r0 + ip];
+    if (bot) {
+        t[2] = o[4];
+        t[5] = o[7];
+        t[6] = o[8];
+    } else {
+        const int64_t rm = (int64_t)wrap_i(j - 1, p.ny) * p.pitch;
+        t[2] = w1 * ((float)base[rm + i] - S0) + (float)base[2 * P + rm + i];
+        t[5] = w5 * ((float)base[rm + im] - S0) + (float)base[5 * P + rm + im];
+        t[6] = w5 * ((float)base[rm + ip] - S0) + (float)base[6 * P + rm + ip];
+    }
+    if (top) {
+        t[4] = o[2];
+        t[7] = o[5];
+        t[8] = o[6];
+    } else {
+        const int64_t rp = (int64_t)wrap_i(j + 1, p.ny) * p.pitch;
+        t[4] = w1 * ((float)base[rp + i] - S0) + (float)base[4 * P + rp + i];
+        t[7] = w5 * ((float)base[rp + ip] - S0) + (float)base[7 * P + rp + ip];
+        t[8] = w5 * ((float)base[rp + im] - S0) + (float)base[8 * P + rp + im];
+    }
+    ScalarMoments m;
+    m.s0 = S0;
+    m.inc = (((t[1] + t[3]) + (t[2] + t[4])) + ((t[5] + t[6]) + (t[7] + t[8]))) -
+            (((o[1] + o[3]) + (o[2] + o[4])) + ((o[5] + o[6]) + (o[7] + o[8])));
+    m.jx = (t[1] - t[3]) + (t[5] - t[6]) - (t[7] - t[8]);
+    m.jy = (t[2] - t[4]) + (t[5] + t[6]) - (t[7] + t[8]);
+    return m;
+}
+
+// Plain post-streaming populations of a lattice in deviation form (for export
+// and re-import), in precision R.
+template <typename R>
+__device__ __forceinline__ void pull9_dev(const float* __restrict__ base, const KParams& p, int i,
+                                          int j, R out[9]) {
+    const int64_t P = p.plane;
+    const int im = wrap_i(i - 1, p.nx), ip = wrap_i(i + 1, p.nx);
+    const int64_t r0 = (int64_t)j * p.pitch;
+    const bool bot = p.walls && j == 0, top = p.walls && j == p.ny - 1;
+    const R S0 = (R)base[r0 + i];
+    R o[9];
+    R osum = 0;
+#pragma unroll
+    for (int q = 1; q < 9; ++q) {
+        o[q] = (R)base[q * P + r0 + i];
+        osum += o[q];
+    }
+    const R w0 = (R)4 / (R)9, w1 = (R)1 / (R)9, w5 = (R)1 / (R)36;
+    out[0] = w0 * S0 - osum;
+    out[1] = w1 * (R)base[r0 + im] + (R)base[1 * P + r0 + im];
+    out[3] = w1 * (R)base[r0 + ip] + (R)base[3 * P + r0 + ip];
+    if (bot) {
+        out[2] = w1 * S0 + o[4];
+        out[5] = w5 * S0 + o[7];
+        out[6] = w5 * S0 + o[8];
+    } else {
+        const int64_t rm = (int64_t)wrap_i(j - 1, p.ny) * p.pitch;
+        out[2] = w1 * (R)base[rm + i] + (R)base[2 * P + rm + i];
+        out[5] = w5 * (R)base[rm + im] + (R)base[5 * P + rm + im];
+        out[6] = w5 * (R)base[rm + ip] + (R)base[6 * P + rm + ip];
+    }
+    if (top) {
+        out[4] = w1 * S0 + o[2];
+        out[7] = w5 * S0 + o[5];
+        out[8] = w5 * S0 + o[6];
+    } else {
+        const int64_t rp = (int64_t)wrap_i(j + 1, p.ny) * p.pitch;
+        out[4] = w1 * (R)base[rp + i] + (R)base[4 * P + rp + i];
+        out[7] = w5 * (R)base[rp + ip] + (R)base[7 * P + rp + ip];
+        out[8] = w5 * (R)base[rp + im] + (R)base[8 * P + rp + im];
+    }
+}
+
+// Error-free sum: hi + lo == a + b exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float& hi, float& lo) {
+    hi = a + b;
+    const float bb = hi - a;
+    lo = (a - (hi - bb)) + (b - bb);
+}
+
+// 32-bit integer hash (avalanche mixer) for the rounding dither.
+__device__ __forceinline__ uint32_t mix32(uint32_t x) {
+    x ^= x >> 16;
+    x *= 0x7feb352du;
+    x ^= x >> 15;
+    x *= 0x846ca68bu;
+    x ^= x >> 16;
+    return x;
+}
+
+__device__ __forceinline__ uint32_t dither_bits(uint32_t step, uint32_t lattice, int64_t cell) {
+    return mix32((uint32_t)cell * 0x9E3779B1u ^ mix32(step * 0x85EBCA77u + lattice * 0xC2B2AE3Du));
+}
+
+// Stochastic rounding of the exact value hi + lo (|lo| <= ulp(hi)/2) to FP32:
+// rounds away from hi towards its neighbour with probability |lo| / gap, so
+// the stored value is unbiased.
+__device__ __forceinline__ float stochastic_round(float hi, float lo, uint32_t bits) {
+    if (lo == 0.0f) return hi;
+    const float nb = nextafterf(hi, lo > 0.0f ? INFINITY : -INFINITY);
+    const float prob = lo / (nb - hi);
+    const float u = (float)(bits >> 8) * (1.0f / 16777216.0f);
+    return u < prob ? nb : hi;
+}
+
 // ---------------------------------------------------------------------------
 // stencils on 3x3 neighbourhoods v[dy+1][dx+1]
 // ---------------------------------------------------------------------------
@@ -202,6 +340,29 @@ __device__ __forceinline__ void collide_scalar(float a[9], float s, float qx, fl
     float r[9];
     central_to_raw(k, ux, uy, r);
     raw_to_pops(r, a);
+}
+
+// Same collision returning deviation-form output: d_q = a~_q - w_q s for
+// q = 1..8 (a~ = P^-1 F^-1(u) k).  The raw moments of the deviation are
+// s (raw moments of the equilibrium shape at u minus those at rest) plus the
+// raw moments of F^-1(u) (0, k10~, k01~, 0, ...), so no O(s) term is formed.
+__device__ __forceinline__ void collide_scalar_dev(float s, float jx, float jy, float qx, float qy,
+                                                   float w, float ux, float uy, float d[9]) {
+    const float k10 = jx - ux * s, k01 = jy - uy * s;
+    const float a = k10 + w * (qx - k10);
+    const float b = k01 + w * (qy - k01);
+    const float ux2 = ux * ux, uy2 = uy * uy, uxy = ux * uy;
+    float R[9];
+    R[0] = 0.0f;
+    R[1] = s * ux + a;
+    R[2] = s * uy + b;
+    R[3] = s * ux2 + 2.0f * ux * a;
+    R[4] = s * uy2 + 2.0f * uy * b;
+    R[5] = s * uxy + uy * a + ux * b;
+    R[6] = s * (ux2 * uy + uy * CS2) + 2.0f * uxy * a + ux2 * b;
+    R[7] = s * (ux * uy2 + ux * CS2) + uy2 * a + 2.0f * uxy * b;
+    R[8] = s * (ux2 * uy2 + CS2 * (ux2 + uy2)) + 2.0f * ux * uy2 * a + 2.0f * ux2 * uy * b;
+    raw_to_pops(R, d);
 }
 
 // Macroscopic inputs of the flow collision at one cell.

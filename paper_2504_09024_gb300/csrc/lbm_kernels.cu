@@ -92,11 +92,14 @@ struct CellOut {
     float ux, uy, dP;
 };
 
-// The three collisions of one cell at row j (in place on f, h, gg).
+// The three collisions of one cell at row j.  f and h enter as their first
+// moments (the zeroth moments are g.phi and g.c) and leave as deviation-form
+// outputs df, dh (q = 1..8); the flow populations gg are collided in place.
 template <bool COUPLED>
 __device__ __forceinline__ CellOut collide_cell(const KParams& p, const CellGeom& g, int j,
-                                                float ux_fixed, float uy_fixed, float f[9],
-                                                float h[9], float gg[9], bool do_collide) {
+                                                float ux_fixed, float uy_fixed, float fjx,
+                                                float fjy, float hjx, float hjy, float gg[9],
+                                                float df[9], float dh[9], bool do_collide) {
     CellOut o;
     // Eq. (theta) and the theta_c of Eq. (ISS)
     const float theta = p.four_over_W * (p.phi_a - g.phi) * (g.phi - p.phi_b) * p.inv_dphi;
@@ -145,11 +148,22 @@ __device__ __forceinline__ CellOut collide_cell(const KParams& p, const CellGeom
         o.dP = 0.0f;
     }
     if (do_collide) {
-        collide_scalar(f, g.phi, p.M_phi * theta * g.nx, p.M_phi * theta * g.ny, p.w_kappa, o.ux,
-                       o.uy);
-        collide_scalar(h, g.c, p.D_s * theta_c * g.nx, p.D_s * theta_c * g.ny, p.w_chi, o.ux, o.uy);
+        collide_scalar_dev(g.phi, fjx, fjy, p.M_phi * theta * g.nx, p.M_phi * theta * g.ny,
+                           p.w_kappa, o.ux, o.uy, df);
+        collide_scalar_dev(g.c, hjx, hjy, p.D_s * theta_c * g.nx, p.D_s * theta_c * g.ny,
+                           p.w_chi, o.ux, o.uy, dh);
     }
     return o;
+}
+
+// Store a deviation-form lattice: plane 0 <- S (stochastically rounded hi + lo),
+// planes 1..8 <- d.
+__device__ __forceinline__ void store_dev(float* __restrict__ base, const KParams& p, int64_t idx,
+                                          float s_hi, float s_lo, const float d[9],
+                                          uint32_t bits) {
+    base[idx] = stochastic_round(s_hi, s_lo, bits);
+#pragma unroll
+    for (int q = 1; q < 9; ++q) base[q * p.plane + idx] = d[q];
 }
 
 __device__ __forceinline__ void store9(float* __restrict__ base, const KParams& p, int64_t idx,
@@ -168,14 +182,14 @@ __global__ void k_fields(KParams p, const float* __restrict__ src, float* __rest
     const int j = blockIdx.y;
     if (i >= p.nx) return;
     const int64_t idx = (int64_t)j * p.pitch + i;
-    float a[9];
-    pull9(src, p, i, j, a);
-    F[FP_PHI * p.plane + idx] = sum9(a);
-    pull9(src + 9 * p.plane, p, i, j, a);
-    const float c = sum9(a);
+    ScalarMoments m = pull_scalar(src, p, i, j);
+    F[FP_PHI * p.plane + idx] = m.s0 + m.inc;
+    m = pull_scalar(src + 9 * p.plane, p, i, j);
+    const float c = m.s0 + m.inc;
     F[FP_C * p.plane + idx] = c;
     F[FP_SIG * p.plane + idx] = sigma_of_c(p, c);
     if (COUPLED) {
+        float a[9];
         pull9(src + 18 * p.plane, p, i, j, a);
         F[FP_DPS * p.plane + idx] = sum9(a);
     }
@@ -232,15 +246,20 @@ __device__ __forceinline__ CellGeom gather_geom(const KParams& p, const float* _
 
 template <bool COUPLED>
 __global__ void k_collide(KParams p, const float* __restrict__ src, float* __restrict__ dst,
-                          const float* __restrict__ F) {
+                          const float* __restrict__ F, uint32_t* __restrict__ ctr, int parity) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y;
+    const uint32_t step = ctr[parity];
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) ctr[1 - parity] = step + 1;
     if (i >= p.nx) return;
     const int64_t idx = (int64_t)j * p.pitch + i;
     CellGeom g = gather_geom<COUPLED>(p, F, i, j);
-    float f[9], h[9], gg[9];
-    pull9(src, p, i, j, f);
-    pull9(src + 9 * p.plane, p, i, j, h);
+    const ScalarMoments mf = pull_scalar(src, p, i, j);
+    const ScalarMoments mh = pull_scalar(src + 9 * p.plane, p, i, j);
+    float fhi, flo, hhi, hlo;
+    two_sum(mf.s0, mf.inc, fhi, flo);
+    two_sum(mh.s0, mh.inc, hhi, hlo);
+    float gg[9], df[9], dh[9];
     float ufx = 0.0f, ufy = 0.0f;
     if (COUPLED) {
         pull9(src + 18 * p.plane, p, i, j, gg);
@@ -248,9 +267,10 @@ __global__ void k_collide(KParams p, const float* __restrict__ src, float* __res
         ufx = F[FP_UX * p.plane + idx];
         ufy = F[FP_UY * p.plane + idx];
     }
-    collide_cell<COUPLED>(p, g, j, ufx, ufy, f, h, gg, true);
-    store9(dst, p, idx, f);
-    store9(dst + 9 * p.plane, p, idx, h);
+    collide_cell<COUPLED>(p, g, j, ufx, ufy, mf.jx, mf.jy, mh.jx, mh.jy, gg, df, dh, true);
+    const int64_t cell = (int64_t)j * p.nx + i;
+    store_dev(dst, p, idx, fhi, flo, df, dither_bits(step, 0, cell));
+    store_dev(dst + 9 * p.plane, p, idx, hhi, hlo, dh, dither_bits(step, 1, cell));
     if (COUPLED) store9(dst + 18 * p.plane, p, idx, gg);
 }
 
@@ -273,7 +293,8 @@ __global__ void k_macro_out(KParams p, const float* __restrict__ src, const floa
         ufx = F[FP_UX * p.plane + idx];
         ufy = F[FP_UY * p.plane + idx];
     }
-    CellOut r = collide_cell<COUPLED>(p, g, j, ufx, ufy, nullptr, nullptr, gg, false);
+    CellOut r = collide_cell<COUPLED>(p, g, j, ufx, ufy, 0.0f, 0.0f, 0.0f, 0.0f, gg, nullptr,
+                                      nullptr, false);
     if (ophi) ophi[o] = g.phi;
     if (oc) oc[o] = g.c;
     if (oux) oux[o] = r.ux;
@@ -285,12 +306,13 @@ __global__ void k_macro_out(KParams p, const float* __restrict__ src, const floa
 // fused sweep kernel
 // ---------------------------------------------------------------------------
 
-constexpr int RING = 5;   // rows kept of phi, c, sigma, P* (current row and four behind)
-constexpr int NRING = 3;  // rows kept of n and |grad phi|
-constexpr int PRING = 3;  // rows of interior populations waiting for their collision
+constexpr int RING = 5;    // rows kept of phi, c, sigma, P* (current row and four behind)
+constexpr int NRING = 3;   // rows kept of n and |grad phi|
+constexpr int PRING = 3;   // rows of interior cells waiting for their collision
+constexpr int PSLOT = 17;  // per waiting cell: f (S hi, lo, jx, jy), h (same), g (9 populations)
 
 size_t fused_smem_bytes(int bx) {
-    return sizeof(float) * (size_t)bx * (4 * RING + 3 * NRING + 27 * PRING);
+    return sizeof(float) * (size_t)bx * (4 * RING + 3 * NRING + PSLOT * PRING);
 }
 
 // Block = bx threads = bx - 4 interior columns plus two halo columns each side.
@@ -300,7 +322,9 @@ size_t fused_smem_bytes(int bx) {
 template <bool COUPLED>
 __global__ void __launch_bounds__(128) k_fused_sweep(KParams p, const float* __restrict__ src,
                                                      float* __restrict__ dst,
-                                                     const float* __restrict__ F, int seg) {
+                                                     const float* __restrict__ F,
+                                                     uint32_t* __restrict__ ctr, int parity,
+                                                     int seg) {
     extern __shared__ float sm[];
     const int bx = blockDim.x;
     const int t = threadIdx.x;
@@ -311,7 +335,10 @@ __global__ void __launch_bounds__(128) k_fused_sweep(KParams p, const float* __r
     float* s_nx = s_dps + RING * bx;         // [NRING][bx]
     float* s_ny = s_nx + NRING * bx;
     float* s_gm = s_ny + NRING * bx;
-    float* s_pop = s_gm + NRING * bx;        // [PRING][27][bx]
+    float* s_pop = s_gm + NRING * bx;        // [PRING][PSLOT][bx]
+
+    const uint32_t step = ctr[parity];
+    if (blockIdx.x == 0 && blockIdx.y == 0 && t == 0) ctr[1 - parity] = step + 1;
 
     const int tx = bx - 4;
     const int x0 = blockIdx.x * tx;
@@ -325,40 +352,42 @@ __global__ void __launch_bounds__(128) k_fused_sweep(KParams p, const float* __r
     else if (col == x0 - 1 || col == xend) role = 2;
     else if (col == x0 - 2 || col == xend + 1) role = 1;
     const int i = wrap_i(col, p.nx);
-    const int nl = COUPLED ? 27 : 18;
-
-    float ufx = 0.0f, ufy = 0.0f;
 
     for (int r = y0 - 2; r <= y1 + 1; ++r) {
         // A: stream row r and form its moments
         const int slot = (r + 2 * RING) % RING;
         if (role > 0) {
             const int jj = ext_row(r, p.ny, p.walls);
-            float a[9];
-            pull9(src, p, i, jj, a);
-            const float phi = sum9(a);
-            s_phi[slot * bx + t] = phi;
-            const bool interior_row = (r >= y0 && r < y1);
-            float* pp = s_pop + ((r + 3 * PRING) % PRING) * 27 * bx;
-            if (role == 3 && interior_row) {
-#pragma unroll
-                for (int q = 0; q < 9; ++q) pp[q * bx + t] = a[q];
+            const bool keep = role == 3 && r >= y0 && r < y1;
+            float* pp = s_pop + ((r + 3 * PRING) % PRING) * PSLOT * bx;
+            ScalarMoments m = pull_scalar(src, p, i, jj);
+            float hi, lo;
+            two_sum(m.s0, m.inc, hi, lo);
+            s_phi[slot * bx + t] = hi;
+            if (keep) {
+                pp[0 * bx + t] = hi;
+                pp[1 * bx + t] = lo;
+                pp[2 * bx + t] = m.jx;
+                pp[3 * bx + t] = m.jy;
             }
             if (role >= 2 && r >= y0 - 1 && r <= y1) {
-                pull9(src + 9 * p.plane, p, i, jj, a);
-                const float c = sum9(a);
-                s_c[slot * bx + t] = c;
-                s_sig[slot * bx + t] = sigma_of_c(p, c);
-                if (role == 3 && interior_row) {
-#pragma unroll
-                    for (int q = 0; q < 9; ++q) pp[(9 + q) * bx + t] = a[q];
+                m = pull_scalar(src + 9 * p.plane, p, i, jj);
+                two_sum(m.s0, m.inc, hi, lo);
+                s_c[slot * bx + t] = hi;
+                s_sig[slot * bx + t] = sigma_of_c(p, hi);
+                if (keep) {
+                    pp[4 * bx + t] = hi;
+                    pp[5 * bx + t] = lo;
+                    pp[6 * bx + t] = m.jx;
+                    pp[7 * bx + t] = m.jy;
                 }
                 if (COUPLED) {
+                    float a[9];
                     pull9(src + 18 * p.plane, p, i, jj, a);
                     s_dps[slot * bx + t] = sum9(a);
-                    if (role == 3 && interior_row) {
+                    if (keep) {
 #pragma unroll
-                        for (int q = 0; q < 9; ++q) pp[(18 + q) * bx + t] = a[q];
+                        for (int q = 0; q < 9; ++q) pp[(8 + q) * bx + t] = a[q];
                     }
                 }
             }
@@ -433,25 +462,26 @@ __global__ void __launch_bounds__(128) k_fused_sweep(KParams p, const float* __r
                 g.dps = 0.0f;
                 g.kappa = g.sgx = g.sgy = g.pgx = g.pgy = g.fgx = g.fgy = 0.0f;
             }
-            const float* pp = s_pop + ((jc + 3 * PRING) % PRING) * 27 * bx;
-            float f[9], h[9], gg[9];
+            const float* pp = s_pop + ((jc + 3 * PRING) % PRING) * PSLOT * bx;
+            const float fhi = pp[0 * bx + t], flo = pp[1 * bx + t];
+            const float fjx = pp[2 * bx + t], fjy = pp[3 * bx + t];
+            const float hhi = pp[4 * bx + t], hlo = pp[5 * bx + t];
+            const float hjx = pp[6 * bx + t], hjy = pp[7 * bx + t];
+            float gg[9], df[9], dh[9];
 #pragma unroll
-            for (int q = 0; q < 9; ++q) {
-                f[q] = pp[q * bx + t];
-                h[q] = pp[(9 + q) * bx + t];
-                gg[q] = COUPLED ? pp[(18 + q) * bx + t] : 0.0f;
-            }
+            for (int q = 0; q < 9; ++q) gg[q] = COUPLED ? pp[(8 + q) * bx + t] : 0.0f;
             const int64_t idx = (int64_t)jc * p.pitch + i;
+            float ufx = 0.0f, ufy = 0.0f;
             if (!COUPLED) {
                 ufx = F[FP_UX * p.plane + idx];
                 ufy = F[FP_UY * p.plane + idx];
             }
-            collide_cell<COUPLED>(p, g, jc, ufx, ufy, f, h, gg, true);
-            store9(dst, p, idx, f);
-            store9(dst + 9 * p.plane, p, idx, h);
+            collide_cell<COUPLED>(p, g, jc, ufx, ufy, fjx, fjy, hjx, hjy, gg, df, dh, true);
+            const int64_t cell = (int64_t)jc * p.nx + i;
+            store_dev(dst, p, idx, fhi, flo, df, dither_bits(step, 0, cell));
+            store_dev(dst + 9 * p.plane, p, idx, hhi, hlo, dh, dither_bits(step, 1, cell));
             if (COUPLED) store9(dst + 18 * p.plane, p, idx, gg);
         }
-        (void)nl;
     }
 }
 
@@ -511,7 +541,9 @@ __global__ void k_init_pre(KParams p, const float* __restrict__ F, float* __rest
 
 // Stored (post-collision, pull-ready) form from post-streaming populations:
 // slot q at y is read by the pull of cell y + e_q, or, when y + e_q lies
-// beyond a wall, by the bounce-back of direction opp(q) at y.
+// beyond a wall, by the bounce-back of direction opp(q) at y.  The two
+// advection-diffusion lattices are then written in deviation form
+// (S = sum of the slots, d_q = slot_q - w_q S); the flow lattice as is.
 __global__ void k_unstream(KParams p, int nlat, const float* __restrict__ pre,
                            float* __restrict__ dst) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -521,22 +553,33 @@ __global__ void k_unstream(KParams p, int nlat, const float* __restrict__ pre,
     for (int l = 0; l < nlat; ++l) {
         const float* pl = pre + (int64_t)l * 9 * p.plane;
         float* dl = dst + (int64_t)l * 9 * p.plane;
+        float u[9];
 #pragma unroll
         for (int q = 0; q < 9; ++q) {
             const int ti = wrap_i(i + ex(q), p.nx);
             const int tj = j + ey(q);
-            float v;
             if (p.walls && (tj < 0 || tj >= p.ny)) {
-                v = pl[opp(q) * p.plane + idx];
+                u[q] = pl[opp(q) * p.plane + idx];
             } else {
-                v = pl[q * p.plane + (int64_t)wrap_i(tj, p.ny) * p.pitch + ti];
+                u[q] = pl[q * p.plane + (int64_t)wrap_i(tj, p.ny) * p.pitch + ti];
             }
-            dl[q * p.plane + idx] = v;
+        }
+        if (l < 2) {
+            double S = 0.0;
+#pragma unroll
+            for (int q = 0; q < 9; ++q) S += (double)u[q];
+            dl[idx] = (float)S;
+#pragma unroll
+            for (int q = 1; q < 9; ++q)
+                dl[q * p.plane + idx] = (float)((double)u[q] - (double)wq(q) * S);
+        } else {
+#pragma unroll
+            for (int q = 0; q < 9; ++q) dl[q * p.plane + idx] = u[q];
         }
     }
 }
 
-// Post-streaming populations of the stored state (pulled), into a pitched float buffer.
+// Post-streaming populations of the stored state, into a pitched float buffer.
 __global__ void k_pull_pre(KParams p, int nlat, const float* __restrict__ src,
                            float* __restrict__ pre) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -545,29 +588,39 @@ __global__ void k_pull_pre(KParams p, int nlat, const float* __restrict__ src,
     const int64_t idx = (int64_t)j * p.pitch + i;
     for (int l = 0; l < nlat; ++l) {
         float a[9];
-        pull9(src + (int64_t)l * 9 * p.plane, p, i, j, a);
+        if (l < 2)
+            pull9_dev<float>(src + (int64_t)l * 9 * p.plane, p, i, j, a);
+        else
+            pull9(src + (int64_t)l * 9 * p.plane, p, i, j, a);
         store9(pre + (int64_t)l * 9 * p.plane, p, idx, a);
     }
 }
 
-// Pitched float pre-form <-> dense float64 host layout, unshifting g.
-__global__ void k_pre_to_f64(KParams p, int nlat, const float* __restrict__ pre,
-                             double* __restrict__ out) {
+// Post-streaming populations as float64 dense [nlat*9][ny][nx], unshifted.
+__global__ void k_export_pops(KParams p, int nlat, const float* __restrict__ src,
+                              double* __restrict__ out) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y;
     if (i >= p.nx) return;
-    const int64_t idx = (int64_t)j * p.pitch + i;
     const int64_t n = (int64_t)p.nx * p.ny;
     const int64_t o = (int64_t)j * p.nx + i;
-    for (int l = 0; l < nlat; ++l)
+    for (int l = 0; l < nlat; ++l) {
+        double a[9];
+        if (l < 2) {
+            pull9_dev<double>(src + (int64_t)l * 9 * p.plane, p, i, j, a);
+        } else {
+            float b[9];
+            pull9(src + (int64_t)l * 9 * p.plane, p, i, j, b);
 #pragma unroll
-        for (int q = 0; q < 9; ++q) {
-            double v = pre[(l * 9 + q) * p.plane + idx];
-            if (l == 2) v += (double)wq(q) * (double)p.P0;
-            out[(l * 9 + q) * n + o] = v;
+            for (int q = 0; q < 9; ++q) a[q] = (double)b[q] + (double)wq(q) * (double)p.P0;
         }
+#pragma unroll
+        for (int q = 0; q < 9; ++q) out[(l * 9 + q) * n + o] = a[q];
+    }
 }
 
+// One lattice of float64 dense post-streaming populations into the pitched
+// float pre-form (flow lattice shifted by w P0).
 __global__ void k_f64_to_pre(KParams p, int lat, const double* __restrict__ in,
                              float* __restrict__ pre) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -756,9 +809,11 @@ void launch_step_split(const KParams& p, const DevState& s, int src, cudaStream_
     launch_fields(p, s, src, st);
     const int bx = 128;
     if (p.coupled)
-        k_collide<true><<<row_grid(p, bx), bx, 0, st>>>(p, s.pop[src], s.pop[1 - src], s.fields);
+        k_collide<true><<<row_grid(p, bx), bx, 0, st>>>(p, s.pop[src], s.pop[1 - src], s.fields,
+                                                        s.counter, src);
     else
-        k_collide<false><<<row_grid(p, bx), bx, 0, st>>>(p, s.pop[src], s.pop[1 - src], s.fields);
+        k_collide<false><<<row_grid(p, bx), bx, 0, st>>>(p, s.pop[src], s.pop[1 - src], s.fields,
+                                                         s.counter, src);
 }
 
 void launch_step_fused(const KParams& p, const DevState& s, int src, const FusedShape& sh,
@@ -768,10 +823,10 @@ void launch_step_fused(const KParams& p, const DevState& s, int src, const Fused
     const size_t smem = fused_smem_bytes(sh.bx);
     if (p.coupled)
         k_fused_sweep<true><<<grid, sh.bx, smem, st>>>(p, s.pop[src], s.pop[1 - src], s.fields,
-                                                      sh.seg);
+                                                      s.counter, src, sh.seg);
     else
         k_fused_sweep<false><<<grid, sh.bx, smem, st>>>(p, s.pop[src], s.pop[1 - src], s.fields,
-                                                       sh.seg);
+                                                       s.counter, src, sh.seg);
 }
 
 cudaError_t configure_fused_smem() {
@@ -808,9 +863,7 @@ void launch_init(const KParams& p, const DevState& s, int dst, const double* phi
 
 void launch_get_pops(const KParams& p, const DevState& s, int src, double* out, cudaStream_t st) {
     const int bx = 128;
-    float* tmp = s.pop[1 - src];
-    k_pull_pre<<<row_grid(p, bx), bx, 0, st>>>(p, s.nlat, s.pop[src], tmp);
-    k_pre_to_f64<<<row_grid(p, bx), bx, 0, st>>>(p, s.nlat, tmp, out);
+    k_export_pops<<<row_grid(p, bx), bx, 0, st>>>(p, s.nlat, s.pop[src], out);
 }
 
 void launch_set_pops(const KParams& p, const DevState& s, int dst, const double* f,
