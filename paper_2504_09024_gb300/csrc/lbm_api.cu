@@ -137,6 +137,18 @@ lbm::KParams make_kparams(const lbm_params& p) {
     k.P0 = (float)(0.5 * (p.rho_a + p.rho_b) / 3.0);
     k.four_over_W = (float)(4.0 / p.W);
     k.eight_over_W = (float)(8.0 / p.W);
+    // fixed-point zeroth moments: 2^29 units per 2^e, with 2^e >= the largest
+    // bound, so values within twice the bounds differ by less than 2^31
+    const double bounds[2] = {std::fmax(std::fabs(p.phi_a), std::fabs(p.phi_b)), p.c_max};
+    for (int l = 0; l < 2; ++l) {
+        const int e = bounds[l] > 1.0 ? (int)std::ceil(std::log2(bounds[l])) : 0;
+        const double scale = std::ldexp(1.0, 29 - e);
+        k.fx_scale[l] = (float)scale;
+        k.fx_inv[l] = (float)(1.0 / scale);
+    }
+    k.phi_a_fx = (int)std::llround(p.phi_a * k.fx_scale[0]);
+    k.phi_b_fx = (int)std::llround(p.phi_b * k.fx_scale[0]);
+    k.phi_m_fx = (int)std::llround(0.5 * (p.phi_a + p.phi_b) * k.fx_scale[0]);
     return k;
 }
 
@@ -238,8 +250,7 @@ int lbm_create(const lbm_params* p, void* stream, lbm_ctx** out) {
         cudaMalloc(&ctx->ds.pop[1], pop_bytes) != cudaSuccess ||
         cudaMalloc(&ctx->ds.fields, fld_bytes) != cudaSuccess ||
         cudaMalloc(&ctx->dpartial, sizeof(double) * lbm::DIAG_NSUM * ctx->diag_nb) != cudaSuccess ||
-        cudaMalloc(&ctx->dresult, sizeof(double) * 16) != cudaSuccess ||
-        cudaMalloc(&ctx->ds.counter, sizeof(uint32_t) * 2) != cudaSuccess) {
+        cudaMalloc(&ctx->dresult, sizeof(double) * 16) != cudaSuccess) {
         cudaGetLastError();
         lbm_destroy(ctx);
         return LBM_ERR_NOMEM;
@@ -248,7 +259,6 @@ int lbm_create(const lbm_params* p, void* stream, lbm_ctx** out) {
     cudaMemsetAsync(ctx->ds.pop[0], 0, pop_bytes, ctx->stream);
     cudaMemsetAsync(ctx->ds.pop[1], 0, pop_bytes, ctx->stream);
     cudaMemsetAsync(ctx->ds.fields, 0, fld_bytes, ctx->stream);
-    cudaMemsetAsync(ctx->ds.counter, 0, sizeof(uint32_t) * 2, ctx->stream);
     if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
         lbm_destroy(ctx);
         return LBM_ERR_CUDA;
@@ -267,7 +277,6 @@ void lbm_destroy(lbm_ctx* ctx) {
     cudaFree(ctx->stage);
     cudaFree(ctx->dpartial);
     cudaFree(ctx->dresult);
-    cudaFree(ctx->ds.counter);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
@@ -277,7 +286,6 @@ int lbm_init_fields_device(lbm_ctx* ctx, const double* phi, const double* c, con
                            const double* uy, const double* P) {
     if (!ctx || !phi || !c || !ux || !uy) return LBM_ERR_INVALID_ARG;
     lbm::launch_init(ctx->kp, ctx->ds, 0, phi, c, ux, uy, P, ctx->stream);
-    cudaMemsetAsync(ctx->ds.counter, 0, sizeof(uint32_t) * 2, ctx->stream);
     ctx->cur = 0;
     ctx->step = 0;
     return check_launch(ctx);
@@ -497,16 +505,9 @@ int lbm_save_state(lbm_ctx* ctx, const char* path) {
     }
     int32_t ver = LBM_ABI_VERSION;
     uint64_t np = pop_n, nv = vel_n;
-    uint32_t ctr[2] = {0, 0};
-    if (cudaMemcpy(ctr, ctx->ds.counter, sizeof(ctr), cudaMemcpyDeviceToHost) != cudaSuccess) {
-        std::fclose(fp);
-        std::free(host);
-        return cuda_fail(ctx, cudaGetLastError());
-    }
-    const uint32_t step_ctr = ctr[ctx->cur];
     bool ok = std::fwrite(kMagic, 1, 8, fp) == 8 && std::fwrite(&ver, 4, 1, fp) == 1 &&
               std::fwrite(&ctx->prm, sizeof(lbm_params), 1, fp) == 1 &&
-              std::fwrite(&ctx->step, 8, 1, fp) == 1 && std::fwrite(&step_ctr, 4, 1, fp) == 1 &&
+              std::fwrite(&ctx->step, 8, 1, fp) == 1 &&
               std::fwrite(&np, 8, 1, fp) == 1 &&
               std::fwrite(&nv, 8, 1, fp) == 1 &&
               std::fwrite(host, sizeof(float), pop_n + vel_n, fp) == pop_n + vel_n;
@@ -525,12 +526,11 @@ int lbm_load_state(lbm_ctx* ctx, const char* path) {
     int32_t ver = 0;
     lbm_params prm;
     int64_t step = 0;
-    uint32_t step_ctr = 0;
     uint64_t np = 0, nv = 0;
     bool ok = std::fread(magic, 1, 8, fp) == 8 && std::memcmp(magic, kMagic, 8) == 0 &&
               std::fread(&ver, 4, 1, fp) == 1 && ver == LBM_ABI_VERSION &&
               std::fread(&prm, sizeof(lbm_params), 1, fp) == 1 &&
-              std::fread(&step, 8, 1, fp) == 1 && std::fread(&step_ctr, 4, 1, fp) == 1 &&
+              std::fread(&step, 8, 1, fp) == 1 &&
               std::fread(&np, 8, 1, fp) == 1 &&
               std::fread(&nv, 8, 1, fp) == 1;
     if (!ok) {
@@ -562,10 +562,6 @@ int lbm_load_state(lbm_ctx* ctx, const char* path) {
         e = cudaMemcpy(ctx->ds.fields + lbm::FP_UX * ctx->kp.plane, host + pop_n,
                        sizeof(float) * vel_n, cudaMemcpyHostToDevice);
     std::free(host);
-    if (e == cudaSuccess) {
-        uint32_t ctr[2] = {step_ctr, step_ctr};
-        e = cudaMemcpy(ctx->ds.counter, ctr, sizeof(ctr), cudaMemcpyHostToDevice);
-    }
     if (e != cudaSuccess) return cuda_fail(ctx, e);
     ctx->step = step;
     return LBM_OK;

@@ -7,13 +7,16 @@
 //
 // Storage: post-collision state, SoA planes [lattice][q][ny][pitch], read by a
 // pull.  Both advection-diffusion lattices (f, h) are kept in deviation form:
-// plane 0 holds the post-collision zeroth moment S (= phi or c) and planes
-// 1..8 hold d_q = a~_q - w_q S (the rest deviation is -sum d_q).  S is written
-// with unbiased stochastic rounding: a slowly evolving interface changes S by
-// less than half an FP32 ulp per step, which round-to-nearest would drop every
-// step.  The flow lattice is stored as g - w_q P0 (P0 = cs2 * reference
-// density) so that FP32 keeps the O(u) information of g; every flow-lattice
-// quantity below is a deviation from the rest state P0 w.
+// plane 0 holds the post-collision zeroth moment S (= phi or c) as a 32-bit
+// fixed-point integer (resolution 2^-29 for values of order one) and planes
+// 1..8 hold FP32 deviations d_q = a~_q - w_q S (the rest deviation is
+// -sum d_q).  Fixed point keeps the slow interface dynamics: an FP32 S would
+// drop increments below half an ulp every step, and S near phi_a = 1 would
+// lose the phi_a - phi that the sharpening flux depends on.  Differences of S
+// between neighbours are exact integer subtractions.  The flow lattice is
+// stored as g - w_q P0 (P0 = cs2 * reference density) so that FP32 keeps the
+// O(u) information of g; every flow-lattice quantity below is a deviation from
+// the rest state P0 w.
 #pragma once
 
 #include <cstdint>
@@ -54,6 +57,9 @@ struct KParams {
     float fext_x, fext_y;
     float P0;               // rest pressure of the shifted flow storage
     float four_over_W, eight_over_W;
+    // fixed-point zeroth moments: value = S * fx_inv[l] (l = 0: phi, 1: c)
+    float fx_scale[2], fx_inv[2];
+    int phi_a_fx, phi_b_fx, phi_m_fx;  // phi_a, phi_b, phi_m in phi fixed point
 };
 
 // ---------------------------------------------------------------------------
@@ -124,35 +130,42 @@ __device__ __forceinline__ void pull9(const T* __restrict__ base, const KParams&
 // and  sum_q e_q a_q(x) = sum_{q>=1} e_q [w_q (S(x-e_q) - S(x)) + d_q(x-e_q)].
 // A source beyond a wall is the cell's own opposite slot (bounce-back).
 struct ScalarMoments {
-    float s0;    // S(x)
-    float inc;   // zeroth moment = s0 + inc
+    int s0;      // S(x), fixed point
+    float inc;   // zeroth moment = s0 * inv_scale + inc
     float jx, jy;
 };
 
-template <typename T>
-__device__ __forceinline__ ScalarMoments pull_scalar(const T* __restrict__ base, const KParams& p,
-                                                     int i, int j) {
+__device__ __forceinline__ int fx_load(const float* p) { return __float_as_int(*p); }
+
+// Fixed-point value after adding a float increment.
+__device__ __forceinline__ int fx_add(int s0, float inc, float scale) {
+    return s0 + __float2int_rn(inc * scale);
+}
+
+__device__ __forceinline__ ScalarMoments pull_scalar(const float* __restrict__ base,
+                                                     const KParams& p, int l, int i, int j) {
     const int64_t P = p.plane;
     const int im = wrap_i(i - 1, p.nx), ip = wrap_i(i + 1, p.nx);
     const int64_t r0 = (int64_t)j * p.pitch;
     const bool bot = p.walls && j == 0, top = p.walls && j == p.ny - 1;
-    const float S0 = (float)base[r0 + i];
+    const int S0 = fx_load(base + r0 + i);
+    const float inv = p.fx_inv[l];
     float o[9];
 #pragma unroll
-    for (int q = 1; q < 9; ++q) o[q] = (float)base[q * P + r0 + i];
-    const float w1 = 1.0f / 9.0f, w5 = 1.0f / 36.0f;
+    for (int q = 1; q < 9; ++q) o[q] = base[q * P + r0 + i];
+    const float w1 = (1.0f / 9.0f) * inv, w5 = (1.0f / 36.0f) * inv;
     float t[9];
-    t[1] = w1 * ((float)base[r0 + im] - S0) + (float)base[1 * P + r0 + im];
-    t[3] = w1 * ((float)base[r0 + ip] - S0) + (float)base[3 * P + r0 + ip];
+    t[1] = w1 * (float)(fx_load(base + r0 + im) - S0) + base[1 * P + r0 + im];
+    t[3] = w1 * (float)(fx_load(base + r0 + ip) - S0) + base[3 * P + r0 + ip];
     if (bot) {
         t[2] = o[4];
         t[5] = o[7];
         t[6] = o[8];
     } else {
         const int64_t rm = (int64_t)wrap_i(j - 1, p.ny) * p.pitch;
-        t[2] = w1 * ((float)base[rm + i] - S0) + (float)base[2 * P + rm + i];
-        t[5] = w5 * ((float)base[rm + im] - S0) + (float)base[5 * P + rm + im];
-        t[6] = w5 * ((float)base[rm + ip] - S0) + (float)base[6 * P + rm + ip];
+        t[2] = w1 * (float)(fx_load(base + rm + i) - S0) + base[2 * P + rm + i];
+        t[5] = w5 * (float)(fx_load(base + rm + im) - S0) + base[5 * P + rm + im];
+        t[6] = w5 * (float)(fx_load(base + rm + ip) - S0) + base[6 * P + rm + ip];
     }
     if (top) {
         t[4] = o[2];
@@ -160,9 +173,9 @@ __device__ __forceinline__ ScalarMoments pull_scalar(const T* __restrict__ base,
         t[8] = o[6];
     } else {
         const int64_t rp = (int64_t)wrap_i(j + 1, p.ny) * p.pitch;
-        t[4] = w1 * ((float)base[rp + i] - S0) + (float)base[4 * P + rp + i];
-        t[7] = w5 * ((float)base[rp + ip] - S0) + (float)base[7 * P + rp + ip];
-        t[8] = w5 * ((float)base[rp + im] - S0) + (float)base[8 * P + rp + im];
+        t[4] = w1 * (float)(fx_load(base + rp + i) - S0) + base[4 * P + rp + i];
+        t[7] = w5 * (float)(fx_load(base + rp + ip) - S0) + base[7 * P + rp + ip];
+        t[8] = w5 * (float)(fx_load(base + rp + im) - S0) + base[8 * P + rp + im];
     }
     ScalarMoments m;
     m.s0 = S0;
@@ -176,13 +189,14 @@ __device__ __forceinline__ ScalarMoments pull_scalar(const T* __restrict__ base,
 // Plain post-streaming populations of a lattice in deviation form (for export
 // and re-import), in precision R.
 template <typename R>
-__device__ __forceinline__ void pull9_dev(const float* __restrict__ base, const KParams& p, int i,
-                                          int j, R out[9]) {
+__device__ __forceinline__ void pull9_dev(const float* __restrict__ base, const KParams& p, int l,
+                                          int i, int j, R out[9]) {
     const int64_t P = p.plane;
     const int im = wrap_i(i - 1, p.nx), ip = wrap_i(i + 1, p.nx);
     const int64_t r0 = (int64_t)j * p.pitch;
     const bool bot = p.walls && j == 0, top = p.walls && j == p.ny - 1;
-    const R S0 = (R)base[r0 + i];
+    const R inv = (R)1 / (R)p.fx_scale[l];
+    const R S0 = (R)fx_load(base + r0 + i) * inv;
     R o[9];
     R osum = 0;
 #pragma unroll
@@ -192,17 +206,17 @@ __device__ __forceinline__ void pull9_dev(const float* __restrict__ base, const 
     }
     const R w0 = (R)4 / (R)9, w1 = (R)1 / (R)9, w5 = (R)1 / (R)36;
     out[0] = w0 * S0 - osum;
-    out[1] = w1 * (R)base[r0 + im] + (R)base[1 * P + r0 + im];
-    out[3] = w1 * (R)base[r0 + ip] + (R)base[3 * P + r0 + ip];
+    out[1] = w1 * (R)fx_load(base + r0 + im) * inv + (R)base[1 * P + r0 + im];
+    out[3] = w1 * (R)fx_load(base + r0 + ip) * inv + (R)base[3 * P + r0 + ip];
     if (bot) {
         out[2] = w1 * S0 + o[4];
         out[5] = w5 * S0 + o[7];
         out[6] = w5 * S0 + o[8];
     } else {
         const int64_t rm = (int64_t)wrap_i(j - 1, p.ny) * p.pitch;
-        out[2] = w1 * (R)base[rm + i] + (R)base[2 * P + rm + i];
-        out[5] = w5 * (R)base[rm + im] + (R)base[5 * P + rm + im];
-        out[6] = w5 * (R)base[rm + ip] + (R)base[6 * P + rm + ip];
+        out[2] = w1 * (R)fx_load(base + rm + i) * inv + (R)base[2 * P + rm + i];
+        out[5] = w5 * (R)fx_load(base + rm + im) * inv + (R)base[5 * P + rm + im];
+        out[6] = w5 * (R)fx_load(base + rm + ip) * inv + (R)base[6 * P + rm + ip];
     }
     if (top) {
         out[4] = w1 * S0 + o[2];
@@ -210,42 +224,31 @@ __device__ __forceinline__ void pull9_dev(const float* __restrict__ base, const 
         out[8] = w5 * S0 + o[6];
     } else {
         const int64_t rp = (int64_t)wrap_i(j + 1, p.ny) * p.pitch;
-        out[4] = w1 * (R)base[rp + i] + (R)base[4 * P + rp + i];
-        out[7] = w5 * (R)base[rp + ip] + (R)base[7 * P + rp + ip];
-        out[8] = w5 * (R)base[rp + im] + (R)base[8 * P + rp + im];
+        out[4] = w1 * (R)fx_load(base + rp + i) * inv + (R)base[4 * P + rp + i];
+        out[7] = w5 * (R)fx_load(base + rp + ip) * inv + (R)base[7 * P + rp + ip];
+        out[8] = w5 * (R)fx_load(base + rp + im) * inv + (R)base[8 * P + rp + im];
     }
 }
 
-// Error-free sum: hi + lo == a + b exactly.
-__device__ __forceinline__ void two_sum(float a, float b, float& hi, float& lo) {
-    hi = a + b;
-    const float bb = hi - a;
-    lo = (a - (hi - bb)) + (b - bb);
+// Isotropic gradient of a fixed-point field from exact integer differences.
+__device__ __forceinline__ void iso_grad_fx(const int v[3][3], float inv, float& gx, float& gy) {
+    gx = ((1.0f / 3.0f) * (float)(v[1][2] - v[1][0]) +
+          (1.0f / 12.0f) * ((float)(v[2][2] - v[2][0]) + (float)(v[0][2] - v[0][0]))) * inv;
+    gy = ((1.0f / 3.0f) * (float)(v[2][1] - v[0][1]) +
+          (1.0f / 12.0f) * ((float)(v[2][2] - v[0][2]) + (float)(v[2][0] - v[0][0]))) * inv;
 }
 
-// 32-bit integer hash (avalanche mixer) for the rounding dither.
-__device__ __forceinline__ uint32_t mix32(uint32_t x) {
-    x ^= x >> 16;
-    x *= 0x7feb352du;
-    x ^= x >> 15;
-    x *= 0x846ca68bu;
-    x ^= x >> 16;
-    return x;
-}
-
-__device__ __forceinline__ uint32_t dither_bits(uint32_t step, uint32_t lattice, int64_t cell) {
-    return mix32((uint32_t)cell * 0x9E3779B1u ^ mix32(step * 0x85EBCA77u + lattice * 0xC2B2AE3Du));
-}
-
-// Stochastic rounding of the exact value hi + lo (|lo| <= ulp(hi)/2) to FP32:
-// rounds away from hi towards its neighbour with probability |lo| / gap, so
-// the stored value is unbiased.
-__device__ __forceinline__ float stochastic_round(float hi, float lo, uint32_t bits) {
-    if (lo == 0.0f) return hi;
-    const float nb = nextafterf(hi, lo > 0.0f ? INFINITY : -INFINITY);
-    const float prob = lo / (nb - hi);
-    const float u = (float)(bits >> 8) * (1.0f / 16777216.0f);
-    return u < prob ? nb : hi;
+// theta (Eq. theta) and theta_c (Eq. ISS) from the fixed-point phi: the
+// factors phi_a - phi, phi - phi_b and phi_m - phi are exact integer
+// differences before the conversion to float.
+__device__ __forceinline__ void interface_coeffs(const KParams& p, int phi_fx, float c, float& theta,
+                                                 float& theta_c) {
+    const float inv = p.fx_inv[0];
+    const float A = (float)(p.phi_a_fx - phi_fx) * inv;
+    const float B = (float)(phi_fx - p.phi_b_fx) * inv;
+    const float M = (float)(p.phi_m_fx - phi_fx) * inv;
+    theta = p.four_over_W * A * B * p.inv_dphi;
+    theta_c = p.eight_over_W * c * M * p.inv_dphi;
 }
 
 // ---------------------------------------------------------------------------

@@ -16,7 +16,6 @@ enum FieldPlane {
 struct DevState {
     float* pop[2];          // ping-pong population buffers [nlat*9][ny][pitch]
     float* fields;          // FP_COUNT planes
-    uint32_t* counter;      // step counters [2] (ping-pong by buffer parity) for the rounding dither
     int nlat;               // 2 (fixed velocity) or 3 (coupled)
 };
 

@@ -78,8 +78,21 @@ __device__ __forceinline__ void load3x3(const float* __restrict__ F, const KPara
     }
 }
 
+__device__ __forceinline__ void load3x3_fx(const float* __restrict__ F, const KParams& p, int i,
+                                           int j, int v[3][3]) {
+    const int im = wrap_i(i - 1, p.nx), ip = wrap_i(i + 1, p.nx);
+#pragma unroll
+    for (int dy = -1; dy <= 1; ++dy) {
+        const int64_t r = (int64_t)ext_row(j + dy, p.ny, p.walls) * p.pitch;
+        v[dy + 1][0] = __float_as_int(F[r + im]);
+        v[dy + 1][1] = __float_as_int(F[r + i]);
+        v[dy + 1][2] = __float_as_int(F[r + ip]);
+    }
+}
+
 // Local values and stencil results one cell's collisions need.
 struct CellGeom {
+    int phi_fx;                  // phi in fixed point (exact interface factors)
     float phi, c, sig, dps;      // zeroth moments, sigma(c), P* - P0
     float nx, ny, gm;            // unit normal, |grad phi|
     float kappa;                 // div n
@@ -102,8 +115,8 @@ __device__ __forceinline__ CellOut collide_cell(const KParams& p, const CellGeom
                                                 float df[9], float dh[9], bool do_collide) {
     CellOut o;
     // Eq. (theta) and the theta_c of Eq. (ISS)
-    const float theta = p.four_over_W * (p.phi_a - g.phi) * (g.phi - p.phi_b) * p.inv_dphi;
-    const float theta_c = p.eight_over_W * g.c * (p.phi_m - g.phi) * p.inv_dphi;
+    float theta, theta_c;
+    interface_coeffs(p, g.phi_fx, g.c, theta, theta_c);
     if (COUPLED) {
         // surface-tension force, Eq. (Fs)
         const float g2 = g.gm * g.gm;
@@ -114,10 +127,12 @@ __device__ __forceinline__ CellOut collide_cell(const KParams& p, const CellGeom
         const float rho = p.rho_uniform ? p.rho_a : lerp_phase(p, g.phi, p.rho_a, p.rho_b);
         const float jx = (gg[1] - gg[3]) + (gg[5] - gg[6]) - (gg[7] - gg[8]);
         const float jy = (gg[2] - gg[4]) + (gg[5] + gg[6]) - (gg[7] + gg[8]);
-        // cs2 rho u = sum e g + cs2 F_t / 2  (App. D)
-        const float inv_rho = 1.0f / rho;
-        o.ux = (3.0f * jx + 0.5f * Ftx) * inv_rho;
-        o.uy = (3.0f * jy + 0.5f * Fty) * inv_rho;
+        // cs2 rho u = sum e g + cs2 F_t / 2  (App. D).  The division uses the
+        // same rounded rho cs2 as the equilibrium, so j -> u -> rho cs2 u does
+        // not drift by the rounding of 1/3 every step.
+        const float R = rho * CS2;
+        o.ux = (jx + 0.5f * CS2 * Ftx) / R;
+        o.uy = (jy + 0.5f * CS2 * Fty) / R;
         // F_p = -grad psi with psi = P* - rho cs2
         float Fpx = -g.pgx, Fpy = -g.pgy;
         if (!p.rho_uniform) {
@@ -156,12 +171,10 @@ __device__ __forceinline__ CellOut collide_cell(const KParams& p, const CellGeom
     return o;
 }
 
-// Store a deviation-form lattice: plane 0 <- S (stochastically rounded hi + lo),
-// planes 1..8 <- d.
+// Store a deviation-form lattice: plane 0 <- S (fixed point), planes 1..8 <- d.
 __device__ __forceinline__ void store_dev(float* __restrict__ base, const KParams& p, int64_t idx,
-                                          float s_hi, float s_lo, const float d[9],
-                                          uint32_t bits) {
-    base[idx] = stochastic_round(s_hi, s_lo, bits);
+                                          int s_fx, const float d[9]) {
+    base[idx] = __int_as_float(s_fx);
 #pragma unroll
     for (int q = 1; q < 9; ++q) base[q * p.plane + idx] = d[q];
 }
@@ -182,12 +195,12 @@ __global__ void k_fields(KParams p, const float* __restrict__ src, float* __rest
     const int j = blockIdx.y;
     if (i >= p.nx) return;
     const int64_t idx = (int64_t)j * p.pitch + i;
-    ScalarMoments m = pull_scalar(src, p, i, j);
-    F[FP_PHI * p.plane + idx] = m.s0 + m.inc;
-    m = pull_scalar(src + 9 * p.plane, p, i, j);
-    const float c = m.s0 + m.inc;
-    F[FP_C * p.plane + idx] = c;
-    F[FP_SIG * p.plane + idx] = sigma_of_c(p, c);
+    ScalarMoments m = pull_scalar(src, p, 0, i, j);
+    F[FP_PHI * p.plane + idx] = __int_as_float(fx_add(m.s0, m.inc, p.fx_scale[0]));
+    m = pull_scalar(src + 9 * p.plane, p, 1, i, j);
+    const int c_fx = fx_add(m.s0, m.inc, p.fx_scale[1]);
+    F[FP_C * p.plane + idx] = __int_as_float(c_fx);
+    F[FP_SIG * p.plane + idx] = sigma_of_c(p, (float)c_fx * p.fx_inv[1]);
     if (COUPLED) {
         float a[9];
         pull9(src + 18 * p.plane, p, i, j, a);
@@ -200,10 +213,10 @@ __global__ void k_normals(KParams p, float* __restrict__ F) {
     const int j = blockIdx.y;
     if (i >= p.nx) return;
     const int64_t idx = (int64_t)j * p.pitch + i;
-    float v[3][3];
-    load3x3(F + FP_PHI * p.plane, p, i, j, v);
+    int v[3][3];
+    load3x3_fx(F + FP_PHI * p.plane, p, i, j, v);
     float gx, gy, nx, ny, gm;
-    iso_grad(v, gx, gy);
+    iso_grad_fx(v, p.fx_inv[0], gx, gy);
     unit_normal(gx, gy, nx, ny, gm);
     F[FP_NX * p.plane + idx] = nx;
     F[FP_NY * p.plane + idx] = ny;
@@ -215,8 +228,9 @@ __device__ __forceinline__ CellGeom gather_geom(const KParams& p, const float* _
                                                 int j) {
     const int64_t idx = (int64_t)j * p.pitch + i;
     CellGeom g;
-    g.phi = F[FP_PHI * p.plane + idx];
-    g.c = F[FP_C * p.plane + idx];
+    g.phi_fx = __float_as_int(F[FP_PHI * p.plane + idx]);
+    g.phi = (float)g.phi_fx * p.fx_inv[0];
+    g.c = (float)__float_as_int(F[FP_C * p.plane + idx]) * p.fx_inv[1];
     g.nx = F[FP_NX * p.plane + idx];
     g.ny = F[FP_NY * p.plane + idx];
     g.gm = F[FP_GM * p.plane + idx];
@@ -232,8 +246,9 @@ __device__ __forceinline__ CellGeom gather_geom(const KParams& p, const float* _
         load3x3(F + FP_DPS * p.plane, p, i, j, v);
         iso_grad(v, g.pgx, g.pgy);
         if (!p.rho_uniform) {
-            load3x3(F + FP_PHI * p.plane, p, i, j, v);
-            iso_grad(v, g.fgx, g.fgy);
+            int vi[3][3];
+            load3x3_fx(F + FP_PHI * p.plane, p, i, j, vi);
+            iso_grad_fx(vi, p.fx_inv[0], g.fgx, g.fgy);
         } else {
             g.fgx = g.fgy = 0.0f;
         }
@@ -246,19 +261,16 @@ __device__ __forceinline__ CellGeom gather_geom(const KParams& p, const float* _
 
 template <bool COUPLED>
 __global__ void k_collide(KParams p, const float* __restrict__ src, float* __restrict__ dst,
-                          const float* __restrict__ F, uint32_t* __restrict__ ctr, int parity) {
+                          const float* __restrict__ F) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y;
-    const uint32_t step = ctr[parity];
-    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) ctr[1 - parity] = step + 1;
     if (i >= p.nx) return;
     const int64_t idx = (int64_t)j * p.pitch + i;
     CellGeom g = gather_geom<COUPLED>(p, F, i, j);
-    const ScalarMoments mf = pull_scalar(src, p, i, j);
-    const ScalarMoments mh = pull_scalar(src + 9 * p.plane, p, i, j);
-    float fhi, flo, hhi, hlo;
-    two_sum(mf.s0, mf.inc, fhi, flo);
-    two_sum(mh.s0, mh.inc, hhi, hlo);
+    const ScalarMoments mf = pull_scalar(src, p, 0, i, j);
+    const ScalarMoments mh = pull_scalar(src + 9 * p.plane, p, 1, i, j);
+    const int f_fx = fx_add(mf.s0, mf.inc, p.fx_scale[0]);
+    const int h_fx = fx_add(mh.s0, mh.inc, p.fx_scale[1]);
     float gg[9], df[9], dh[9];
     float ufx = 0.0f, ufy = 0.0f;
     if (COUPLED) {
@@ -268,9 +280,8 @@ __global__ void k_collide(KParams p, const float* __restrict__ src, float* __res
         ufy = F[FP_UY * p.plane + idx];
     }
     collide_cell<COUPLED>(p, g, j, ufx, ufy, mf.jx, mf.jy, mh.jx, mh.jy, gg, df, dh, true);
-    const int64_t cell = (int64_t)j * p.nx + i;
-    store_dev(dst, p, idx, fhi, flo, df, dither_bits(step, 0, cell));
-    store_dev(dst + 9 * p.plane, p, idx, hhi, hlo, dh, dither_bits(step, 1, cell));
+    store_dev(dst, p, idx, f_fx, df);
+    store_dev(dst + 9 * p.plane, p, idx, h_fx, dh);
     if (COUPLED) store9(dst + 18 * p.plane, p, idx, gg);
 }
 
@@ -295,8 +306,8 @@ __global__ void k_macro_out(KParams p, const float* __restrict__ src, const floa
     }
     CellOut r = collide_cell<COUPLED>(p, g, j, ufx, ufy, 0.0f, 0.0f, 0.0f, 0.0f, gg, nullptr,
                                       nullptr, false);
-    if (ophi) ophi[o] = g.phi;
-    if (oc) oc[o] = g.c;
+    if (ophi) ophi[o] = (double)g.phi_fx / (double)p.fx_scale[0];
+    if (oc) oc[o] = (double)__float_as_int(F[FP_C * p.plane + idx]) / (double)p.fx_scale[1];
     if (oux) oux[o] = r.ux;
     if (ouy) ouy[o] = r.uy;
     if (oP) oP[o] = COUPLED ? (double)p.P0 + (double)r.dP : 0.0;
@@ -309,7 +320,7 @@ __global__ void k_macro_out(KParams p, const float* __restrict__ src, const floa
 constexpr int RING = 5;    // rows kept of phi, c, sigma, P* (current row and four behind)
 constexpr int NRING = 3;   // rows kept of n and |grad phi|
 constexpr int PRING = 3;   // rows of interior cells waiting for their collision
-constexpr int PSLOT = 17;  // per waiting cell: f (S hi, lo, jx, jy), h (same), g (9 populations)
+constexpr int PSLOT = 15;  // per waiting cell: f (jx, jy), h (S, jx, jy), g (9 populations)
 
 size_t fused_smem_bytes(int bx) {
     return sizeof(float) * (size_t)bx * (4 * RING + 3 * NRING + PSLOT * PRING);
@@ -322,23 +333,18 @@ size_t fused_smem_bytes(int bx) {
 template <bool COUPLED>
 __global__ void __launch_bounds__(128) k_fused_sweep(KParams p, const float* __restrict__ src,
                                                      float* __restrict__ dst,
-                                                     const float* __restrict__ F,
-                                                     uint32_t* __restrict__ ctr, int parity,
-                                                     int seg) {
+                                                     const float* __restrict__ F, int seg) {
     extern __shared__ float sm[];
     const int bx = blockDim.x;
     const int t = threadIdx.x;
-    float* s_phi = sm;                       // [RING][bx]
-    float* s_c = s_phi + RING * bx;
+    int* s_phi = reinterpret_cast<int*>(sm);  // [RING][bx] phi, fixed point
+    float* s_c = sm + RING * bx;
     float* s_sig = s_c + RING * bx;
     float* s_dps = s_sig + RING * bx;
     float* s_nx = s_dps + RING * bx;         // [NRING][bx]
     float* s_ny = s_nx + NRING * bx;
     float* s_gm = s_ny + NRING * bx;
     float* s_pop = s_gm + NRING * bx;        // [PRING][PSLOT][bx]
-
-    const uint32_t step = ctr[parity];
-    if (blockIdx.x == 0 && blockIdx.y == 0 && t == 0) ctr[1 - parity] = step + 1;
 
     const int tx = bx - 4;
     const int x0 = blockIdx.x * tx;
@@ -360,26 +366,22 @@ __global__ void __launch_bounds__(128) k_fused_sweep(KParams p, const float* __r
             const int jj = ext_row(r, p.ny, p.walls);
             const bool keep = role == 3 && r >= y0 && r < y1;
             float* pp = s_pop + ((r + 3 * PRING) % PRING) * PSLOT * bx;
-            ScalarMoments m = pull_scalar(src, p, i, jj);
-            float hi, lo;
-            two_sum(m.s0, m.inc, hi, lo);
-            s_phi[slot * bx + t] = hi;
+            ScalarMoments m = pull_scalar(src, p, 0, i, jj);
+            s_phi[slot * bx + t] = fx_add(m.s0, m.inc, p.fx_scale[0]);
             if (keep) {
-                pp[0 * bx + t] = hi;
-                pp[1 * bx + t] = lo;
-                pp[2 * bx + t] = m.jx;
-                pp[3 * bx + t] = m.jy;
+                pp[0 * bx + t] = m.jx;
+                pp[1 * bx + t] = m.jy;
             }
             if (role >= 2 && r >= y0 - 1 && r <= y1) {
-                m = pull_scalar(src + 9 * p.plane, p, i, jj);
-                two_sum(m.s0, m.inc, hi, lo);
-                s_c[slot * bx + t] = hi;
-                s_sig[slot * bx + t] = sigma_of_c(p, hi);
+                m = pull_scalar(src + 9 * p.plane, p, 1, i, jj);
+                const int c_fx = fx_add(m.s0, m.inc, p.fx_scale[1]);
+                const float c = (float)c_fx * p.fx_inv[1];
+                s_c[slot * bx + t] = c;
+                s_sig[slot * bx + t] = sigma_of_c(p, c);
                 if (keep) {
-                    pp[4 * bx + t] = hi;
-                    pp[5 * bx + t] = lo;
-                    pp[6 * bx + t] = m.jx;
-                    pp[7 * bx + t] = m.jy;
+                    pp[2 * bx + t] = __int_as_float(c_fx);
+                    pp[3 * bx + t] = m.jx;
+                    pp[4 * bx + t] = m.jy;
                 }
                 if (COUPLED) {
                     float a[9];
@@ -387,7 +389,7 @@ __global__ void __launch_bounds__(128) k_fused_sweep(KParams p, const float* __r
                     s_dps[slot * bx + t] = sum9(a);
                     if (keep) {
 #pragma unroll
-                        for (int q = 0; q < 9; ++q) pp[(8 + q) * bx + t] = a[q];
+                        for (int q = 0; q < 9; ++q) pp[(6 + q) * bx + t] = a[q];
                     }
                 }
             }
@@ -398,12 +400,12 @@ __global__ void __launch_bounds__(128) k_fused_sweep(KParams p, const float* __r
         if (role >= 2 && rn >= y0 - 1 && rn <= y1) {
             const int sm1 = (rn - 1 + 2 * RING) % RING, s0 = (rn + 2 * RING) % RING,
                       sp1 = (rn + 1 + 2 * RING) % RING;
-            float v[3][3];
+            int v[3][3];
             v[0][0] = s_phi[sm1 * bx + t - 1]; v[0][1] = s_phi[sm1 * bx + t]; v[0][2] = s_phi[sm1 * bx + t + 1];
             v[1][0] = s_phi[s0 * bx + t - 1];  v[1][1] = s_phi[s0 * bx + t];  v[1][2] = s_phi[s0 * bx + t + 1];
             v[2][0] = s_phi[sp1 * bx + t - 1]; v[2][1] = s_phi[sp1 * bx + t]; v[2][2] = s_phi[sp1 * bx + t + 1];
             float gx, gy, nx, ny, gm;
-            iso_grad(v, gx, gy);
+            iso_grad_fx(v, p.fx_inv[0], gx, gy);
             unit_normal(gx, gy, nx, ny, gm);
             const int ns = (rn + 3 * NRING) % NRING;
             s_nx[ns * bx + t] = nx;
@@ -419,7 +421,8 @@ __global__ void __launch_bounds__(128) k_fused_sweep(KParams p, const float* __r
             const int nm1 = (jc - 1 + 3 * NRING) % NRING, n0 = (jc + 3 * NRING) % NRING,
                       np1 = (jc + 1 + 3 * NRING) % NRING;
             CellGeom g;
-            g.phi = s_phi[c0 * bx + t];
+            g.phi_fx = s_phi[c0 * bx + t];
+            g.phi = (float)g.phi_fx * p.fx_inv[0];
             g.c = s_c[c0 * bx + t];
             g.sig = s_sig[c0 * bx + t];
             g.nx = s_nx[n0 * bx + t];
@@ -450,11 +453,12 @@ __global__ void __launch_bounds__(128) k_fused_sweep(KParams p, const float* __r
                     for (int e = 0; e < 3; ++e) v[d][e] = s_dps[cr[d] * bx + t - 1 + e];
                 iso_grad(v, g.pgx, g.pgy);
                 if (!p.rho_uniform) {
+                    int vi[3][3];
 #pragma unroll
                     for (int d = 0; d < 3; ++d)
 #pragma unroll
-                        for (int e = 0; e < 3; ++e) v[d][e] = s_phi[cr[d] * bx + t - 1 + e];
-                    iso_grad(v, g.fgx, g.fgy);
+                        for (int e = 0; e < 3; ++e) vi[d][e] = s_phi[cr[d] * bx + t - 1 + e];
+                    iso_grad_fx(vi, p.fx_inv[0], g.fgx, g.fgy);
                 } else {
                     g.fgx = g.fgy = 0.0f;
                 }
@@ -463,13 +467,12 @@ __global__ void __launch_bounds__(128) k_fused_sweep(KParams p, const float* __r
                 g.kappa = g.sgx = g.sgy = g.pgx = g.pgy = g.fgx = g.fgy = 0.0f;
             }
             const float* pp = s_pop + ((jc + 3 * PRING) % PRING) * PSLOT * bx;
-            const float fhi = pp[0 * bx + t], flo = pp[1 * bx + t];
-            const float fjx = pp[2 * bx + t], fjy = pp[3 * bx + t];
-            const float hhi = pp[4 * bx + t], hlo = pp[5 * bx + t];
-            const float hjx = pp[6 * bx + t], hjy = pp[7 * bx + t];
+            const float fjx = pp[0 * bx + t], fjy = pp[1 * bx + t];
+            const int h_fx = __float_as_int(pp[2 * bx + t]);
+            const float hjx = pp[3 * bx + t], hjy = pp[4 * bx + t];
             float gg[9], df[9], dh[9];
 #pragma unroll
-            for (int q = 0; q < 9; ++q) gg[q] = COUPLED ? pp[(8 + q) * bx + t] : 0.0f;
+            for (int q = 0; q < 9; ++q) gg[q] = COUPLED ? pp[(6 + q) * bx + t] : 0.0f;
             const int64_t idx = (int64_t)jc * p.pitch + i;
             float ufx = 0.0f, ufy = 0.0f;
             if (!COUPLED) {
@@ -477,9 +480,8 @@ __global__ void __launch_bounds__(128) k_fused_sweep(KParams p, const float* __r
                 ufy = F[FP_UY * p.plane + idx];
             }
             collide_cell<COUPLED>(p, g, jc, ufx, ufy, fjx, fjy, hjx, hjy, gg, df, dh, true);
-            const int64_t cell = (int64_t)jc * p.nx + i;
-            store_dev(dst, p, idx, fhi, flo, df, dither_bits(step, 0, cell));
-            store_dev(dst + 9 * p.plane, p, idx, hhi, hlo, dh, dither_bits(step, 1, cell));
+            store_dev(dst, p, idx, g.phi_fx, df);
+            store_dev(dst + 9 * p.plane, p, idx, h_fx, dh);
             if (COUPLED) store9(dst + 18 * p.plane, p, idx, gg);
         }
     }
@@ -500,8 +502,8 @@ __global__ void k_init_fields(KParams p, const double* __restrict__ phi,
     const int64_t o = (int64_t)j * p.nx + i;
     const float fphi = (float)phi[o];
     const float fc = (float)c[o];
-    F[FP_PHI * p.plane + idx] = fphi;
-    F[FP_C * p.plane + idx] = fc;
+    F[FP_PHI * p.plane + idx] = __int_as_float(__double2int_rn(phi[o] * (double)p.fx_scale[0]));
+    F[FP_C * p.plane + idx] = __int_as_float(__double2int_rn(c[o] * (double)p.fx_scale[1]));
     F[FP_SIG * p.plane + idx] = sigma_of_c(p, fc);
     F[FP_UX * p.plane + idx] = (float)ux[o];
     F[FP_UY * p.plane + idx] = (float)uy[o];
@@ -519,14 +521,15 @@ __global__ void k_init_pre(KParams p, const float* __restrict__ F, float* __rest
     const int j = blockIdx.y;
     if (i >= p.nx) return;
     const int64_t idx = (int64_t)j * p.pitch + i;
-    const float phi = F[FP_PHI * p.plane + idx];
-    const float c = F[FP_C * p.plane + idx];
+    const int phi_fx = __float_as_int(F[FP_PHI * p.plane + idx]);
+    const float phi = (float)phi_fx * p.fx_inv[0];
+    const float c = (float)__float_as_int(F[FP_C * p.plane + idx]) * p.fx_inv[1];
     const float nx = F[FP_NX * p.plane + idx];
     const float ny = F[FP_NY * p.plane + idx];
     const float ux = F[FP_UX * p.plane + idx];
     const float uy = F[FP_UY * p.plane + idx];
-    const float theta = p.four_over_W * (p.phi_a - phi) * (phi - p.phi_b) * p.inv_dphi;
-    const float theta_c = p.eight_over_W * c * (p.phi_m - phi) * p.inv_dphi;
+    float theta, theta_c;
+    interface_coeffs(p, phi_fx, c, theta, theta_c);
     float a[9];
     eq_scalar(a, phi, p.M_phi * theta * nx, p.M_phi * theta * ny, ux, uy);
     store9(pre, p, idx, a);
@@ -568,10 +571,12 @@ __global__ void k_unstream(KParams p, int nlat, const float* __restrict__ pre,
             double S = 0.0;
 #pragma unroll
             for (int q = 0; q < 9; ++q) S += (double)u[q];
-            dl[idx] = (float)S;
+            const int S_fx = __double2int_rn(S * (double)p.fx_scale[l]);
+            const double Sr = (double)S_fx / (double)p.fx_scale[l];
+            dl[idx] = __int_as_float(S_fx);
 #pragma unroll
             for (int q = 1; q < 9; ++q)
-                dl[q * p.plane + idx] = (float)((double)u[q] - (double)wq(q) * S);
+                dl[q * p.plane + idx] = (float)((double)u[q] - (double)wq(q) * Sr);
         } else {
 #pragma unroll
             for (int q = 0; q < 9; ++q) dl[q * p.plane + idx] = u[q];
@@ -589,7 +594,7 @@ __global__ void k_pull_pre(KParams p, int nlat, const float* __restrict__ src,
     for (int l = 0; l < nlat; ++l) {
         float a[9];
         if (l < 2)
-            pull9_dev<float>(src + (int64_t)l * 9 * p.plane, p, i, j, a);
+            pull9_dev<float>(src + (int64_t)l * 9 * p.plane, p, l, i, j, a);
         else
             pull9(src + (int64_t)l * 9 * p.plane, p, i, j, a);
         store9(pre + (int64_t)l * 9 * p.plane, p, idx, a);
@@ -607,7 +612,7 @@ __global__ void k_export_pops(KParams p, int nlat, const float* __restrict__ src
     for (int l = 0; l < nlat; ++l) {
         double a[9];
         if (l < 2) {
-            pull9_dev<double>(src + (int64_t)l * 9 * p.plane, p, i, j, a);
+            pull9_dev<double>(src + (int64_t)l * 9 * p.plane, p, l, i, j, a);
         } else {
             float b[9];
             pull9(src + (int64_t)l * 9 * p.plane, p, i, j, b);
@@ -809,11 +814,9 @@ void launch_step_split(const KParams& p, const DevState& s, int src, cudaStream_
     launch_fields(p, s, src, st);
     const int bx = 128;
     if (p.coupled)
-        k_collide<true><<<row_grid(p, bx), bx, 0, st>>>(p, s.pop[src], s.pop[1 - src], s.fields,
-                                                        s.counter, src);
+        k_collide<true><<<row_grid(p, bx), bx, 0, st>>>(p, s.pop[src], s.pop[1 - src], s.fields);
     else
-        k_collide<false><<<row_grid(p, bx), bx, 0, st>>>(p, s.pop[src], s.pop[1 - src], s.fields,
-                                                         s.counter, src);
+        k_collide<false><<<row_grid(p, bx), bx, 0, st>>>(p, s.pop[src], s.pop[1 - src], s.fields);
 }
 
 void launch_step_fused(const KParams& p, const DevState& s, int src, const FusedShape& sh,
@@ -823,10 +826,10 @@ void launch_step_fused(const KParams& p, const DevState& s, int src, const Fused
     const size_t smem = fused_smem_bytes(sh.bx);
     if (p.coupled)
         k_fused_sweep<true><<<grid, sh.bx, smem, st>>>(p, s.pop[src], s.pop[1 - src], s.fields,
-                                                      s.counter, src, sh.seg);
+                                                      sh.seg);
     else
         k_fused_sweep<false><<<grid, sh.bx, smem, st>>>(p, s.pop[src], s.pop[1 - src], s.fields,
-                                                       s.counter, src, sh.seg);
+                                                       sh.seg);
 }
 
 cudaError_t configure_fused_smem() {
