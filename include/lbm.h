@@ -68,9 +68,10 @@ enum lbm_mode {
 };
 
 enum lbm_kernel {
-    LBM_KERNEL_AUTO = 0,   /* library choice (the fused sweep kernel) */
+    LBM_KERNEL_AUTO = 0,   /* library choice (the TMA-staged sweep) */
     LBM_KERNEL_SPLIT = 1,  /* three-kernel chain: moments, normals, collide */
-    LBM_KERNEL_FUSED = 2   /* one fused stream + collide sweep kernel per step */
+    LBM_KERNEL_FUSED = 2,  /* one fused sweep kernel per step, per-thread loads */
+    LBM_KERNEL_TMA = 3     /* one fused sweep kernel per step, rows staged by bulk-tensor copies */
 };
 
 typedef struct lbm_params {
@@ -170,7 +171,8 @@ int lbm_set_populations(lbm_ctx *ctx, const double *f, const double *h, const do
  * Synchronous.  Returns LBM_OK even when out->status reports non-finite cells. */
 int lbm_diagnostics(lbm_ctx *ctx, lbm_diag *out);
 
-/* Wait for the context stream; report any pending CUDA error. */
+/* Wait for the context stream; report any pending CUDA error, or
+ * LBM_ERR_TIMEOUT if a kernel's bounded wait for a staged row expired. */
 int lbm_synchronize(lbm_ctx *ctx);
 
 /* Steps taken since the last initialisation (-1 for a NULL context). */
@@ -181,9 +183,10 @@ int64_t lbm_get_step(const lbm_ctx *ctx);
 int lbm_kernel_in_use(const lbm_ctx *ctx);
 int lbm_launches_per_step(const lbm_ctx *ctx);
 
-/* Launch shape of the fused kernel: columns per block (tile_x, a multiple of
- * 32 in [64, 512]) and rows per block (seg_y >= 4).  0 keeps the current
- * value.  Errors: INVALID_ARG, UNSUPPORTED (split kernel). */
+/* Launch shape of the sweep kernels: threads per block (tile_x; the block
+ * owns tile_x - 4 columns; 128 for FUSED, 64 or 128 for TMA) and rows per
+ * block (seg_y >= 4).  0 keeps the current value.
+ * Errors: INVALID_ARG, UNSUPPORTED (split kernel, or tile_x not available). */
 int lbm_set_launch_shape(lbm_ctx *ctx, int32_t tile_x, int32_t seg_y);
 int lbm_get_launch_shape(const lbm_ctx *ctx, int32_t *tile_x, int32_t *seg_y);
 
@@ -193,6 +196,14 @@ int lbm_get_launch_shape(const lbm_ctx *ctx, int32_t *tile_x, int32_t *seg_y);
  * Errors: IO, INVALID_ARG (parameter mismatch), CUDA. */
 int lbm_save_state(lbm_ctx *ctx, const char *path);
 int lbm_load_state(lbm_ctx *ctx, const char *path);
+
+/* Test hook for the failure path of the bounded device waits (TMA kernel
+ * only): the next step's kernel waits on a shared-memory barrier that no copy
+ * completes, gives up after a short bound, sets the context's error flag and
+ * returns.  The next synchronising call reports LBM_ERR_TIMEOUT; the context
+ * stays usable but its state is undefined until re-initialised.
+ * Errors: INVALID_ARG, UNSUPPORTED (other kernels). */
+int lbm_debug_stall_next_step(lbm_ctx *ctx);
 
 /* Static description of an error code. */
 const char *lbm_strerror(int code);

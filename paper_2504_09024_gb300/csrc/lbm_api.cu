@@ -24,7 +24,9 @@ constexpr int GRAPH_STEPS = 32;  // steps per captured graph (even: parity prese
 struct lbm_ctx {
     lbm_params prm;
     lbm::KParams kp;
-    lbm::DevState ds;
+    lbm::DevState ds;           // kernel view: pointers to column 0 of each row
+    float* pop_alloc[2] = {nullptr, nullptr};
+    float* fields_alloc = nullptr;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     cudaStream_t cap_stream = nullptr;
@@ -39,6 +41,8 @@ struct lbm_ctx {
     double* dresult = nullptr;
     int diag_nb = 0;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    CUtensorMap tmaps[2];   // bulk-tensor maps over the two population buffers
+    int* derr = nullptr;    // device flag: a bounded wait expired
     int pending_error = LBM_OK;
 };
 
@@ -84,7 +88,7 @@ int validate(const lbm_params* p) {
     if ((int64_t)p->nx * p->ny > (int64_t)1 << 31) return LBM_ERR_INVALID_ARG;
     if (p->walls_y != 0 && p->walls_y != 1) return LBM_ERR_INVALID_ARG;
     if (p->mode != LBM_COUPLED && p->mode != LBM_FIXED_U) return LBM_ERR_INVALID_ARG;
-    if (p->kernel < LBM_KERNEL_AUTO || p->kernel > LBM_KERNEL_FUSED) return LBM_ERR_INVALID_ARG;
+    if (p->kernel < LBM_KERNEL_AUTO || p->kernel > LBM_KERNEL_TMA) return LBM_ERR_INVALID_ARG;
     if (p->reserved != 0) return LBM_ERR_INVALID_ARG;
     if (p->dtype != LBM_F32) {
         if (p->dtype == LBM_F16S || p->dtype == LBM_BF16S) return LBM_ERR_UNSUPPORTED;
@@ -103,7 +107,7 @@ lbm::KParams make_kparams(const lbm_params& p) {
     lbm::KParams k{};
     k.nx = p.nx;
     k.ny = p.ny;
-    k.pitch = (p.nx + 31) / 32 * 32;
+    k.pitch = (p.nx + 2 * lbm::XGHOST + 31) / 32 * 32;
     k.walls = p.walls_y;
     k.coupled = p.mode == LBM_COUPLED;
     k.plane = (int64_t)k.pitch * p.ny;
@@ -155,8 +159,20 @@ lbm::KParams make_kparams(const lbm_params& p) {
 void launch_one_step(lbm_ctx* ctx, int src, cudaStream_t st) {
     if (ctx->kernel == LBM_KERNEL_SPLIT)
         lbm::launch_step_split(ctx->kp, ctx->ds, src, st);
+    else if (ctx->kernel == LBM_KERNEL_TMA)
+        lbm::launch_step_tma(ctx->kp, ctx->ds, src, ctx->shape, ctx->tmaps, ctx->derr, st);
     else
         lbm::launch_step_fused(ctx->kp, ctx->ds, src, ctx->shape, st);
+}
+
+int build_tensor_maps(lbm_ctx* ctx) {
+    if (ctx->kernel != LBM_KERNEL_TMA) return LBM_OK;
+    const int nplanes = ctx->ds.nlat * 9;
+    for (int b = 0; b < 2; ++b)
+        if (!lbm::make_tensor_map(&ctx->tmaps[b], ctx->pop_alloc[b], ctx->kp, nplanes,
+                                  ctx->shape.bx))
+            return LBM_ERR_UNSUPPORTED;
+    return LBM_OK;
 }
 
 int build_graph(lbm_ctx* ctx, int parity) {
@@ -197,6 +213,14 @@ int lbm_params_default(lbm_params* p) {
     return LBM_OK;
 }
 
+int lbm_debug_stall_next_step(lbm_ctx* ctx) {
+    if (!ctx) return LBM_ERR_INVALID_ARG;
+    if (ctx->kernel != LBM_KERNEL_TMA) return LBM_ERR_UNSUPPORTED;
+    ctx->kp.stall_test = 1;
+    drop_graphs(ctx);
+    return LBM_OK;
+}
+
 const char* lbm_strerror(int code) {
     switch (code) {
         case LBM_OK: return "ok";
@@ -222,7 +246,13 @@ int lbm_create(const lbm_params* p, void* stream, lbm_ctx** out) {
     if (!ctx) return LBM_ERR_NOMEM;
     ctx->prm = *p;
     ctx->kp = make_kparams(*p);
-    ctx->kernel = p->kernel == LBM_KERNEL_SPLIT ? LBM_KERNEL_SPLIT : LBM_KERNEL_FUSED;
+    ctx->kernel = p->kernel == LBM_KERNEL_AUTO ? (lbm::tma_available() ? LBM_KERNEL_TMA
+                                                                       : LBM_KERNEL_FUSED)
+                                               : p->kernel;
+    if (ctx->kernel == LBM_KERNEL_TMA && !lbm::tma_available()) {
+        delete ctx;
+        return LBM_ERR_UNSUPPORTED;
+    }
     cudaGetDevice(&ctx->device);
     if (stream) {
         ctx->stream = (cudaStream_t)stream;
@@ -237,7 +267,7 @@ int lbm_create(const lbm_params* p, void* stream, lbm_ctx** out) {
         lbm_destroy(ctx);
         return LBM_ERR_CUDA;
     }
-    if (lbm::configure_fused_smem() != cudaSuccess) {
+    if (lbm::configure_fused_smem() != cudaSuccess || lbm::configure_tma_smem() != cudaSuccess) {
         cudaGetLastError();
         lbm_destroy(ctx);
         return LBM_ERR_CUDA;
@@ -246,19 +276,27 @@ int lbm_create(const lbm_params* p, void* stream, lbm_ctx** out) {
     const size_t pop_bytes = sizeof(float) * (size_t)ctx->ds.nlat * 9 * (size_t)ctx->kp.plane;
     const size_t fld_bytes = sizeof(float) * (size_t)lbm::FP_COUNT * (size_t)ctx->kp.plane;
     ctx->diag_nb = lbm::diag_blocks(ctx->kp);
-    if (cudaMalloc(&ctx->ds.pop[0], pop_bytes) != cudaSuccess ||
-        cudaMalloc(&ctx->ds.pop[1], pop_bytes) != cudaSuccess ||
-        cudaMalloc(&ctx->ds.fields, fld_bytes) != cudaSuccess ||
+    if (cudaMalloc(&ctx->pop_alloc[0], pop_bytes) != cudaSuccess ||
+        cudaMalloc(&ctx->pop_alloc[1], pop_bytes) != cudaSuccess ||
+        cudaMalloc(&ctx->fields_alloc, fld_bytes) != cudaSuccess ||
         cudaMalloc(&ctx->dpartial, sizeof(double) * lbm::DIAG_NSUM * ctx->diag_nb) != cudaSuccess ||
-        cudaMalloc(&ctx->dresult, sizeof(double) * 16) != cudaSuccess) {
+        cudaMalloc(&ctx->dresult, sizeof(double) * 16) != cudaSuccess ||
+        cudaMalloc(&ctx->derr, sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
         lbm_destroy(ctx);
         return LBM_ERR_NOMEM;
     }
     // a defined state before initialisation
-    cudaMemsetAsync(ctx->ds.pop[0], 0, pop_bytes, ctx->stream);
-    cudaMemsetAsync(ctx->ds.pop[1], 0, pop_bytes, ctx->stream);
-    cudaMemsetAsync(ctx->ds.fields, 0, fld_bytes, ctx->stream);
+    for (int b = 0; b < 2; ++b) ctx->ds.pop[b] = ctx->pop_alloc[b] + lbm::XGHOST;
+    ctx->ds.fields = ctx->fields_alloc + lbm::XGHOST;
+    cudaMemsetAsync(ctx->pop_alloc[0], 0, pop_bytes, ctx->stream);
+    cudaMemsetAsync(ctx->pop_alloc[1], 0, pop_bytes, ctx->stream);
+    cudaMemsetAsync(ctx->fields_alloc, 0, fld_bytes, ctx->stream);
+    cudaMemsetAsync(ctx->derr, 0, sizeof(int), ctx->stream);
+    if (build_tensor_maps(ctx) != LBM_OK) {
+        lbm_destroy(ctx);
+        return LBM_ERR_UNSUPPORTED;
+    }
     if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
         lbm_destroy(ctx);
         return LBM_ERR_CUDA;
@@ -271,12 +309,13 @@ void lbm_destroy(lbm_ctx* ctx) {
     if (!ctx) return;
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     drop_graphs(ctx);
-    cudaFree(ctx->ds.pop[0]);
-    cudaFree(ctx->ds.pop[1]);
-    cudaFree(ctx->ds.fields);
+    cudaFree(ctx->pop_alloc[0]);
+    cudaFree(ctx->pop_alloc[1]);
+    cudaFree(ctx->fields_alloc);
     cudaFree(ctx->stage);
     cudaFree(ctx->dpartial);
     cudaFree(ctx->dresult);
+    cudaFree(ctx->derr);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
@@ -318,7 +357,7 @@ int lbm_init_fields(lbm_ctx* ctx, const double* phi, const double* c, const doub
 int lbm_step(lbm_ctx* ctx, int64_t nsteps) {
     if (!ctx || nsteps < 0) return LBM_ERR_INVALID_ARG;
     while (nsteps > 0) {
-        if (nsteps >= GRAPH_STEPS) {
+        if (nsteps >= GRAPH_STEPS && !ctx->kp.stall_test) {
             if (!ctx->graph[ctx->cur]) {
                 int rc = build_graph(ctx, ctx->cur);
                 if (rc != LBM_OK) return rc;
@@ -332,6 +371,10 @@ int lbm_step(lbm_ctx* ctx, int64_t nsteps) {
             ctx->cur ^= 1;
             ctx->step += 1;
             nsteps -= 1;
+            if (ctx->kp.stall_test) {  // one-shot test hook
+                ctx->kp.stall_test = 0;
+                drop_graphs(ctx);
+            }
         }
     }
     return check_launch(ctx);
@@ -443,6 +486,14 @@ int lbm_synchronize(lbm_ctx* ctx) {
     if (e != cudaSuccess) return cuda_fail(ctx, e);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(ctx, e);
+    int timed_out = 0;
+    e = cudaMemcpy(&timed_out, ctx->derr, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(ctx, e);
+    if (timed_out) {
+        cudaMemset(ctx->derr, 0, sizeof(int));
+        ctx->pending_error = LBM_OK;
+        return LBM_ERR_TIMEOUT;
+    }
     int pend = ctx->pending_error;
     ctx->pending_error = LBM_OK;
     return pend;
@@ -459,15 +510,16 @@ int lbm_launches_per_step(const lbm_ctx* ctx) {
 
 int lbm_set_launch_shape(lbm_ctx* ctx, int32_t tile_x, int32_t seg_y) {
     if (!ctx) return LBM_ERR_INVALID_ARG;
-    if (ctx->kernel != LBM_KERNEL_FUSED) return LBM_ERR_UNSUPPORTED;
-    if (tile_x != 0 && tile_x != 128) return tile_x % 32 == 0 && tile_x >= 64 && tile_x <= 512
-                                                 ? LBM_ERR_UNSUPPORTED
-                                                 : LBM_ERR_INVALID_ARG;
+    if (ctx->kernel == LBM_KERNEL_SPLIT) return LBM_ERR_UNSUPPORTED;
+    if (tile_x < 0 || (tile_x != 0 && (tile_x % 32 != 0 || tile_x < 64 || tile_x > 512)))
+        return LBM_ERR_INVALID_ARG;
     if (seg_y != 0 && seg_y < 4) return LBM_ERR_INVALID_ARG;
+    const bool ok_bx = tile_x == 0 || tile_x == 128 || (tile_x == 64 && ctx->kernel == LBM_KERNEL_TMA);
+    if (!ok_bx) return LBM_ERR_UNSUPPORTED;
     if (tile_x) ctx->shape.bx = tile_x;
     if (seg_y) ctx->shape.seg = seg_y;
     drop_graphs(ctx);
-    return LBM_OK;
+    return build_tensor_maps(ctx);
 }
 
 int lbm_get_launch_shape(const lbm_ctx* ctx, int32_t* tile_x, int32_t* seg_y) {
@@ -489,10 +541,10 @@ int lbm_save_state(lbm_ctx* ctx, const char* path) {
     const size_t vel_n = ctx->kp.coupled ? 0 : 2 * (size_t)ctx->kp.plane;
     float* host = (float*)std::malloc(sizeof(float) * (pop_n + vel_n));
     if (!host) return LBM_ERR_NOMEM;
-    cudaError_t e = cudaMemcpy(host, ctx->ds.pop[ctx->cur], sizeof(float) * pop_n,
+    cudaError_t e = cudaMemcpy(host, ctx->pop_alloc[ctx->cur], sizeof(float) * pop_n,
                                cudaMemcpyDeviceToHost);
     if (e == cudaSuccess && vel_n)
-        e = cudaMemcpy(host + pop_n, ctx->ds.fields + lbm::FP_UX * ctx->kp.plane,
+        e = cudaMemcpy(host + pop_n, ctx->fields_alloc + lbm::FP_UX * ctx->kp.plane,
                        sizeof(float) * vel_n, cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) {
         std::free(host);
@@ -556,10 +608,10 @@ int lbm_load_state(lbm_ctx* ctx, const char* path) {
         std::free(host);
         return LBM_ERR_IO;
     }
-    cudaError_t e = cudaMemcpy(ctx->ds.pop[ctx->cur], host, sizeof(float) * pop_n,
+    cudaError_t e = cudaMemcpy(ctx->pop_alloc[ctx->cur], host, sizeof(float) * pop_n,
                                cudaMemcpyHostToDevice);
     if (e == cudaSuccess && vel_n)
-        e = cudaMemcpy(ctx->ds.fields + lbm::FP_UX * ctx->kp.plane, host + pop_n,
+        e = cudaMemcpy(ctx->fields_alloc + lbm::FP_UX * ctx->kp.plane, host + pop_n,
                        sizeof(float) * vel_n, cudaMemcpyHostToDevice);
     std::free(host);
     if (e != cudaSuccess) return cuda_fail(ctx, e);

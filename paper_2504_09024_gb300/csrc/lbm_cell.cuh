@@ -1,0 +1,209 @@
+// Per-cell pieces of the coupled step shared by every step kernel: equilibria,
+// field-plane stencil loads, the three collisions of one cell (Sec. 3, App. C,
+// App. D) and the state stores that keep the periodic ghost columns.
+#pragma once
+
+#include "lbm_internal.h"
+
+namespace lbm {
+
+// ---------------------------------------------------------------------------
+// shared helpers
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ float sum9(const float a[9]) {
+    return ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7])) + a[8];
+}
+
+__device__ __forceinline__ float lerp_phase(const KParams& p, float phi, float va, float vb) {
+    return vb + (phi - p.phi_b) * p.inv_dphi * (va - vb);
+}
+
+__device__ __forceinline__ float rate_from_coeff(float coeff) {
+    return 1.0f / (coeff * 3.0f + 0.5f);
+}
+
+// Deviation-form equilibrium of the flow lattice without source: shifted
+// populations g^eq - w P0 for pressure deviation dP = P - P0.
+__device__ __forceinline__ void eq_flow_shifted(float a[9], float dP, float rho, float ux,
+                                                float uy) {
+    const float ux2 = ux * ux, uy2 = uy * uy, uxy = ux * uy;
+    const float R = rho * CS2, RmP = R - dP;
+    float k[9];
+    k[0] = dP;
+    k[1] = ux * RmP;
+    k[2] = uy * RmP;
+    k[3] = -R * ux2 + dP * (CS2 + ux2);
+    k[4] = -R * uy2 + dP * (CS2 + uy2);
+    k[5] = -RmP * uxy;
+    k[6] = RmP * (ux2 + CS2) * uy;
+    k[7] = RmP * (uy2 + CS2) * ux;
+    k[8] = -R * (ux2 * uy2 + CS2 * (ux2 + uy2)) + dP * (ux2 + CS2) * (uy2 + CS2);
+    float r[9];
+    central_to_raw(k, ux, uy, r);
+    raw_to_pops(r, a);
+}
+
+__device__ __forceinline__ void eq_scalar(float a[9], float s, float qx, float qy, float ux,
+                                          float uy) {
+    float k[9] = {s, qx, qy, CS2 * s, CS2 * s, 0.0f, 0.0f, 0.0f, CS2 * CS2 * s};
+    float r[9];
+    central_to_raw(k, ux, uy, r);
+    raw_to_pops(r, a);
+}
+
+// 3x3 neighbourhood of a field plane on the extended (periodic / mirrored)
+// grid; ysign = -1 flips the sign of mirrored ghost rows (y component of n).
+__device__ __forceinline__ void load3x3(const float* __restrict__ F, const KParams& p, int i, int j,
+                                        float v[3][3], bool odd_under_mirror = false) {
+    const int im = wrap_i(i - 1, p.nx), ip = wrap_i(i + 1, p.nx);
+#pragma unroll
+    for (int dy = -1; dy <= 1; ++dy) {
+        const int jj = j + dy;
+        const int64_t r = (int64_t)ext_row(jj, p.ny, p.walls) * p.pitch;
+        const float s = odd_under_mirror ? mirror_sign(jj, p.ny, p.walls) : 1.0f;
+        v[dy + 1][0] = s * F[r + im];
+        v[dy + 1][1] = s * F[r + i];
+        v[dy + 1][2] = s * F[r + ip];
+    }
+}
+
+__device__ __forceinline__ void load3x3_fx(const float* __restrict__ F, const KParams& p, int i,
+                                           int j, int v[3][3]) {
+    const int im = wrap_i(i - 1, p.nx), ip = wrap_i(i + 1, p.nx);
+#pragma unroll
+    for (int dy = -1; dy <= 1; ++dy) {
+        const int64_t r = (int64_t)ext_row(j + dy, p.ny, p.walls) * p.pitch;
+        v[dy + 1][0] = __float_as_int(F[r + im]);
+        v[dy + 1][1] = __float_as_int(F[r + i]);
+        v[dy + 1][2] = __float_as_int(F[r + ip]);
+    }
+}
+
+// Local values and stencil results one cell's collisions need.
+struct CellGeom {
+    int phi_fx;                  // phi in fixed point (exact interface factors)
+    float phi, c, sig, dps;      // zeroth moments, sigma(c), P* - P0
+    float nx, ny, gm;            // unit normal, |grad phi|
+    float kappa;                 // div n
+    float sgx, sgy;              // grad sigma
+    float pgx, pgy;              // grad (P* - P0)
+    float fgx, fgy;              // grad phi (for grad rho)
+};
+
+struct CellOut {
+    float ux, uy, dP;
+};
+
+// The three collisions of one cell at row j.  f and h enter as their first
+// moments (the zeroth moments are g.phi and g.c) and leave as deviation-form
+// outputs df, dh (q = 1..8); the flow populations gg are collided in place.
+template <bool COUPLED>
+__device__ __forceinline__ CellOut collide_cell(const KParams& p, const CellGeom& g, int j,
+                                                float ux_fixed, float uy_fixed, float fjx,
+                                                float fjy, float hjx, float hjy, float gg[9],
+                                                float df[9], float dh[9], bool do_collide) {
+    CellOut o;
+    // Eq. (theta) and the theta_c of Eq. (ISS)
+    float theta, theta_c;
+    interface_coeffs(p, g.phi_fx, g.c, theta, theta_c);
+    if (COUPLED) {
+        // surface-tension force, Eq. (Fs)
+        const float g2 = g.gm * g.gm;
+        const float nds = g.nx * g.sgx + g.ny * g.sgy;
+        const float Fsx = p.N_sigma * g2 * (-g.sig * g.kappa * g.nx + (g.sgx - g.nx * nds));
+        const float Fsy = p.N_sigma * g2 * (-g.sig * g.kappa * g.ny + (g.sgy - g.ny * nds));
+        const float Ftx = Fsx + p.fext_x, Fty = Fsy + p.fext_y;
+        const float rho = p.rho_uniform ? p.rho_a : lerp_phase(p, g.phi, p.rho_a, p.rho_b);
+        const float jx = (gg[1] - gg[3]) + (gg[5] - gg[6]) - (gg[7] - gg[8]);
+        const float jy = (gg[2] - gg[4]) + (gg[5] + gg[6]) - (gg[7] + gg[8]);
+        // cs2 rho u = sum e g + cs2 F_t / 2  (App. D).  The division uses the
+        // same rounded rho cs2 as the equilibrium, so j -> u -> rho cs2 u does
+        // not drift by the rounding of 1/3 every step.
+        const float R = rho * CS2;
+        o.ux = (jx + 0.5f * CS2 * Ftx) / R;
+        o.uy = (jy + 0.5f * CS2 * Fty) / R;
+        // F_p = -grad psi with psi = P* - rho cs2
+        float Fpx = -g.pgx, Fpy = -g.pgy;
+        if (!p.rho_uniform) {
+            const float drho = (p.rho_a - p.rho_b) * p.inv_dphi;
+            Fpx += CS2 * drho * g.fgx;
+            Fpy += CS2 * drho * g.fgy;
+        }
+        const float G = Fpx * o.ux + Fpy * o.uy;
+        o.dP = g.dps + 0.5f * G;  // P = sum g + sigma_00 / 2
+        if (do_collide) {
+            FlowMacro m;
+            m.ux = o.ux;
+            m.uy = o.uy;
+            m.rho = rho;
+            m.dPs = g.dps;
+            m.dP = o.dP;
+            m.Ftx = Ftx;
+            m.Fty = Fty;
+            m.Fpx = Fpx;
+            m.Fpy = Fpy;
+            m.w_nu = p.nu_uniform ? p.w_nu : rate_from_coeff(lerp_phase(p, g.phi, p.nu_a, p.nu_b));
+            collide_flow(gg, m, p.w_zeta);
+            wall_correct_flow(gg, p, j, rho);
+        }
+    } else {
+        o.ux = ux_fixed;
+        o.uy = uy_fixed;
+        o.dP = 0.0f;
+    }
+    if (do_collide) {
+        collide_scalar_dev(g.phi, fjx, fjy, p.M_phi * theta * g.nx, p.M_phi * theta * g.ny,
+                           p.w_kappa, o.ux, o.uy, df);
+        collide_scalar_dev(g.c, hjx, hjy, p.D_s * theta_c * g.nx, p.D_s * theta_c * g.ny,
+                           p.w_chi, o.ux, o.uy, dh);
+    }
+    return o;
+}
+
+// Offsets of the periodic ghost copies of column i: columns below XGHOST are
+// mirrored to the right ghosts (i + nx), columns from nx - XGHOST to the left
+// ghosts (i - nx); on grids narrower than 2 XGHOST a column has both.
+__device__ __forceinline__ int ghost_right(const KParams& p, int i) { return i < XGHOST ? p.nx : 0; }
+__device__ __forceinline__ int ghost_left(const KParams& p, int i) {
+    return i >= p.nx - XGHOST ? -p.nx : 0;
+}
+
+// Store a deviation-form lattice: plane 0 <- S (fixed point), planes 1..8 <- d;
+// edge columns also refresh their ghost copies.
+__device__ __forceinline__ void store_dev(float* __restrict__ base, const KParams& p, int64_t idx,
+                                          int i, int s_fx, const float d[9]) {
+    const int gs[2] = {ghost_right(p, i), ghost_left(p, i)};
+    base[idx] = __int_as_float(s_fx);
+#pragma unroll
+    for (int q = 1; q < 9; ++q) base[q * p.plane + idx] = d[q];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        if (!gs[k]) continue;
+        base[idx + gs[k]] = __int_as_float(s_fx);
+#pragma unroll
+        for (int q = 1; q < 9; ++q) base[q * p.plane + idx + gs[k]] = d[q];
+    }
+}
+
+__device__ __forceinline__ void store9(float* __restrict__ base, const KParams& p, int64_t idx,
+                                       int i, const float a[9]) {
+    const int gs[2] = {ghost_right(p, i), ghost_left(p, i)};
+#pragma unroll
+    for (int q = 0; q < 9; ++q) base[q * p.plane + idx] = a[q];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        if (!gs[k]) continue;
+#pragma unroll
+        for (int q = 0; q < 9; ++q) base[q * p.plane + idx + gs[k]] = a[q];
+    }
+}
+
+// Plain store for scratch buffers (no ghost copy).
+__device__ __forceinline__ void store9_plain(float* __restrict__ base, const KParams& p,
+                                             int64_t idx, const float a[9]) {
+#pragma unroll
+    for (int q = 0; q < 9; ++q) base[q * p.plane + idx] = a[q];
+}
+
+}  // namespace lbm

@@ -19,6 +19,7 @@
 // the rest state P0 w.
 #pragma once
 
+#include <climits>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -42,6 +43,12 @@ __host__ __device__ constexpr float wq(int q) {
 }
 
 // Kernel parameters (float copies of lbm_params plus derived rates).
+// Row layout: [XGHOST ghost columns | nx columns | XGHOST ghost columns | pad],
+// pitch a multiple of 32 floats.  Kernels receive pointers to column 0; the
+// ghost columns -XGHOST..-1 and nx..nx+XGHOST-1 mirror the periodic images and
+// let bulk-tensor loads read whole rows without wrapping.
+constexpr int XGHOST = 4;
+
 struct KParams {
     int nx, ny, pitch, walls;
     int coupled;
@@ -60,6 +67,7 @@ struct KParams {
     // fixed-point zeroth moments: value = S * fx_inv[l] (l = 0: phi, 1: c)
     float fx_scale[2], fx_inv[2];
     int phi_a_fx, phi_b_fx, phi_m_fx;  // phi_a, phi_b, phi_m in phi fixed point
+    int stall_test;         // test hook: wait on a barrier nothing completes (bounded)
 };
 
 // ---------------------------------------------------------------------------
@@ -86,39 +94,46 @@ __device__ __forceinline__ float mirror_sign(int j, int ny, int walls) {
 // streaming (pull) with half-way bounce-back
 // ---------------------------------------------------------------------------
 
-// Gather the 9 post-streaming populations of cell (i, j) of one lattice from
-// the post-collision planes `base` (q-th plane at base + q * plane): a_q(x) =
-// a~_q(x - e_q); a source beyond a wall is replaced by the cell's own opposite
-// slot, which the writer has already bounce-back corrected.
-template <typename T>
-__device__ __forceinline__ void pull9(const T* __restrict__ base, const KParams& p, int i, int j,
+// Gather the 9 post-streaming populations of one cell of a lattice: a_q(x) =
+// a~_q(x - e_q).  Rm, R0, Rp point at plane 0 of rows j-1, j, j+1; planes are
+// PS elements apart; cm, c0, cp are the columns x-1, x, x+1.  A source beyond
+// a wall (bot: j is the bottom row, top: the top row) is replaced by the
+// cell's own opposite slot, which the writer has already bounce-back
+// corrected.
+__device__ __forceinline__ void pull9_rows(const float* __restrict__ Rm,
+                                           const float* __restrict__ R0,
+                                           const float* __restrict__ Rp, int64_t PS, int cm,
+                                           int c0, int cp, bool bot, bool top, float out[9]) {
+    out[0] = R0[c0];
+    out[1] = R0[1 * PS + cm];
+    out[3] = R0[3 * PS + cp];
+    if (bot) {
+        out[2] = R0[4 * PS + c0];
+        out[5] = R0[7 * PS + c0];
+        out[6] = R0[8 * PS + c0];
+    } else {
+        out[2] = Rm[2 * PS + c0];
+        out[5] = Rm[5 * PS + cm];
+        out[6] = Rm[6 * PS + cp];
+    }
+    if (top) {
+        out[4] = R0[2 * PS + c0];
+        out[7] = R0[5 * PS + c0];
+        out[8] = R0[6 * PS + c0];
+    } else {
+        out[4] = Rp[4 * PS + c0];
+        out[7] = Rp[7 * PS + cp];
+        out[8] = Rp[8 * PS + cm];
+    }
+}
+
+__device__ __forceinline__ void pull9(const float* __restrict__ base, const KParams& p, int i, int j,
                                       float out[9]) {
-    const int64_t P = p.plane;
-    const int im = wrap_i(i - 1, p.nx), ip = wrap_i(i + 1, p.nx);
-    const int64_t r0 = (int64_t)j * p.pitch;
-    out[0] = (float)base[0 * P + r0 + i];
-    out[1] = (float)base[1 * P + r0 + im];
-    out[3] = (float)base[3 * P + r0 + ip];
-    if (p.walls && j == 0) {
-        out[2] = (float)base[4 * P + r0 + i];
-        out[5] = (float)base[7 * P + r0 + i];
-        out[6] = (float)base[8 * P + r0 + i];
-    } else {
-        const int64_t rm = (int64_t)wrap_i(j - 1, p.ny) * p.pitch;
-        out[2] = (float)base[2 * P + rm + i];
-        out[5] = (float)base[5 * P + rm + im];
-        out[6] = (float)base[6 * P + rm + ip];
-    }
-    if (p.walls && j == p.ny - 1) {
-        out[4] = (float)base[2 * P + r0 + i];
-        out[7] = (float)base[5 * P + r0 + i];
-        out[8] = (float)base[6 * P + r0 + i];
-    } else {
-        const int64_t rp = (int64_t)wrap_i(j + 1, p.ny) * p.pitch;
-        out[4] = (float)base[4 * P + rp + i];
-        out[7] = (float)base[7 * P + rp + ip];
-        out[8] = (float)base[8 * P + rp + im];
-    }
+    const bool bot = p.walls && j == 0, top = p.walls && j == p.ny - 1;
+    const float* R0 = base + (int64_t)j * p.pitch;
+    const float* Rm = base + (int64_t)wrap_i(j - 1, p.ny) * p.pitch;
+    const float* Rp = base + (int64_t)wrap_i(j + 1, p.ny) * p.pitch;
+    pull9_rows(Rm, R0, Rp, p.plane, wrap_i(i - 1, p.nx), i, wrap_i(i + 1, p.nx), bot, top, out);
 }
 
 // Zeroth and first moments of the post-streaming populations of a lattice in
@@ -137,45 +152,59 @@ struct ScalarMoments {
 
 __device__ __forceinline__ int fx_load(const float* p) { return __float_as_int(*p); }
 
+// Invalid fixed-point value (the analogue of NaN): produced by non-finite or
+// out-of-range increments and kept by every later addition.
+constexpr int FX_INVALID = INT_MIN;
+constexpr int FX_RANGE = 1 << 30;  // |value| beyond this (twice the bounds) is invalid
+
 // Fixed-point value after adding a float increment.
 __device__ __forceinline__ int fx_add(int s0, float inc, float scale) {
-    return s0 + __float2int_rn(inc * scale);
+    const float v = inc * scale;
+    if (s0 == FX_INVALID || !(fabsf(v) < 1.0e9f)) return FX_INVALID;
+    const int r = s0 + __float2int_rn(v);
+    return (r > FX_RANGE || r < -FX_RANGE) ? FX_INVALID : r;
 }
 
-__device__ __forceinline__ ScalarMoments pull_scalar(const float* __restrict__ base,
-                                                     const KParams& p, int l, int i, int j) {
-    const int64_t P = p.plane;
-    const int im = wrap_i(i - 1, p.nx), ip = wrap_i(i + 1, p.nx);
-    const int64_t r0 = (int64_t)j * p.pitch;
-    const bool bot = p.walls && j == 0, top = p.walls && j == p.ny - 1;
-    const int S0 = fx_load(base + r0 + i);
-    const float inv = p.fx_inv[l];
+// Float value of a fixed-point number (NaN for the invalid marker).
+__device__ __forceinline__ double fx_to_double(int s, float scale) {
+    return s == FX_INVALID ? __longlong_as_double(0x7ff8000000000000ll) : (double)s / (double)scale;
+}
+
+__device__ __forceinline__ int fx_from_double(double v, float scale) {
+    const double x = v * (double)scale;
+    return (isfinite(x) && fabs(x) <= (double)FX_RANGE) ? __double2int_rn(x) : FX_INVALID;
+}
+
+__device__ __forceinline__ ScalarMoments pull_scalar_rows(const float* __restrict__ Rm,
+                                                          const float* __restrict__ R0,
+                                                          const float* __restrict__ Rp,
+                                                          int64_t PS, int cm, int c0, int cp,
+                                                          bool bot, bool top, float inv) {
+    const int S0 = fx_load(R0 + c0);
     float o[9];
 #pragma unroll
-    for (int q = 1; q < 9; ++q) o[q] = base[q * P + r0 + i];
+    for (int q = 1; q < 9; ++q) o[q] = R0[q * PS + c0];
     const float w1 = (1.0f / 9.0f) * inv, w5 = (1.0f / 36.0f) * inv;
     float t[9];
-    t[1] = w1 * (float)(fx_load(base + r0 + im) - S0) + base[1 * P + r0 + im];
-    t[3] = w1 * (float)(fx_load(base + r0 + ip) - S0) + base[3 * P + r0 + ip];
+    t[1] = w1 * (float)(fx_load(R0 + cm) - S0) + R0[1 * PS + cm];
+    t[3] = w1 * (float)(fx_load(R0 + cp) - S0) + R0[3 * PS + cp];
     if (bot) {
         t[2] = o[4];
         t[5] = o[7];
         t[6] = o[8];
     } else {
-        const int64_t rm = (int64_t)wrap_i(j - 1, p.ny) * p.pitch;
-        t[2] = w1 * (float)(fx_load(base + rm + i) - S0) + base[2 * P + rm + i];
-        t[5] = w5 * (float)(fx_load(base + rm + im) - S0) + base[5 * P + rm + im];
-        t[6] = w5 * (float)(fx_load(base + rm + ip) - S0) + base[6 * P + rm + ip];
+        t[2] = w1 * (float)(fx_load(Rm + c0) - S0) + Rm[2 * PS + c0];
+        t[5] = w5 * (float)(fx_load(Rm + cm) - S0) + Rm[5 * PS + cm];
+        t[6] = w5 * (float)(fx_load(Rm + cp) - S0) + Rm[6 * PS + cp];
     }
     if (top) {
         t[4] = o[2];
         t[7] = o[5];
         t[8] = o[6];
     } else {
-        const int64_t rp = (int64_t)wrap_i(j + 1, p.ny) * p.pitch;
-        t[4] = w1 * (float)(fx_load(base + rp + i) - S0) + base[4 * P + rp + i];
-        t[7] = w5 * (float)(fx_load(base + rp + ip) - S0) + base[7 * P + rp + ip];
-        t[8] = w5 * (float)(fx_load(base + rp + im) - S0) + base[8 * P + rp + im];
+        t[4] = w1 * (float)(fx_load(Rp + c0) - S0) + Rp[4 * PS + c0];
+        t[7] = w5 * (float)(fx_load(Rp + cp) - S0) + Rp[7 * PS + cp];
+        t[8] = w5 * (float)(fx_load(Rp + cm) - S0) + Rp[8 * PS + cm];
     }
     ScalarMoments m;
     m.s0 = S0;
@@ -184,6 +213,16 @@ __device__ __forceinline__ ScalarMoments pull_scalar(const float* __restrict__ b
     m.jx = (t[1] - t[3]) + (t[5] - t[6]) - (t[7] - t[8]);
     m.jy = (t[2] - t[4]) + (t[5] + t[6]) - (t[7] + t[8]);
     return m;
+}
+
+__device__ __forceinline__ ScalarMoments pull_scalar(const float* __restrict__ base,
+                                                     const KParams& p, int l, int i, int j) {
+    const bool bot = p.walls && j == 0, top = p.walls && j == p.ny - 1;
+    const float* R0 = base + (int64_t)j * p.pitch;
+    const float* Rm = base + (int64_t)wrap_i(j - 1, p.ny) * p.pitch;
+    const float* Rp = base + (int64_t)wrap_i(j + 1, p.ny) * p.pitch;
+    return pull_scalar_rows(Rm, R0, Rp, p.plane, wrap_i(i - 1, p.nx), i, wrap_i(i + 1, p.nx), bot,
+                            top, p.fx_inv[l]);
 }
 
 // Plain post-streaming populations of a lattice in deviation form (for export
@@ -196,7 +235,7 @@ __device__ __forceinline__ void pull9_dev(const float* __restrict__ base, const 
     const int64_t r0 = (int64_t)j * p.pitch;
     const bool bot = p.walls && j == 0, top = p.walls && j == p.ny - 1;
     const R inv = (R)1 / (R)p.fx_scale[l];
-    const R S0 = (R)fx_load(base + r0 + i) * inv;
+    const R S0 = (R)fx_to_double(fx_load(base + r0 + i), p.fx_scale[l]);
     R o[9];
     R osum = 0;
 #pragma unroll

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "lbm_device.cuh"
@@ -30,6 +31,13 @@ void launch_step_split(const KParams& p, const DevState& s, int src, cudaStream_
 void launch_step_fused(const KParams& p, const DevState& s, int src, const FusedShape& sh,
                        cudaStream_t st);
 size_t fused_smem_bytes(int bx);
+// Fused step with bulk-tensor staging (lbm_sweep_tma.cu).
+bool tma_available();
+bool make_tensor_map(CUtensorMap* map, float* alloc, const KParams& p, int nplanes, int bx);
+size_t tma_smem_bytes(int bx, bool coupled);
+cudaError_t configure_tma_smem();
+void launch_step_tma(const KParams& p, const DevState& s, int src, const FusedShape& sh,
+                     const CUtensorMap* maps, int* err, cudaStream_t st);
 // Fill the field planes (phi, c, dP*, sigma, n, |grad phi|) of the current state.
 void launch_fields(const KParams& p, const DevState& s, int src, cudaStream_t st);
 // Macroscopic outputs (float64, dense [ny][nx]) of the current state; needs launch_fields first.

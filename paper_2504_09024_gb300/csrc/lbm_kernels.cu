@@ -13,177 +13,9 @@
 //  * initialisation, population import/export and FP64 reductions.
 #include <cmath>
 
-#include "lbm_internal.h"
+#include "lbm_cell.cuh"
 
 namespace lbm {
-
-// ---------------------------------------------------------------------------
-// shared helpers
-// ---------------------------------------------------------------------------
-
-__device__ __forceinline__ float sum9(const float a[9]) {
-    return ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7])) + a[8];
-}
-
-__device__ __forceinline__ float lerp_phase(const KParams& p, float phi, float va, float vb) {
-    return vb + (phi - p.phi_b) * p.inv_dphi * (va - vb);
-}
-
-__device__ __forceinline__ float rate_from_coeff(float coeff) {
-    return 1.0f / (coeff * 3.0f + 0.5f);
-}
-
-// Deviation-form equilibrium of the flow lattice without source: shifted
-// populations g^eq - w P0 for pressure deviation dP = P - P0.
-__device__ __forceinline__ void eq_flow_shifted(float a[9], float dP, float rho, float ux,
-                                                float uy) {
-    const float ux2 = ux * ux, uy2 = uy * uy, uxy = ux * uy;
-    const float R = rho * CS2, RmP = R - dP;
-    float k[9];
-    k[0] = dP;
-    k[1] = ux * RmP;
-    k[2] = uy * RmP;
-    k[3] = -R * ux2 + dP * (CS2 + ux2);
-    k[4] = -R * uy2 + dP * (CS2 + uy2);
-    k[5] = -RmP * uxy;
-    k[6] = RmP * (ux2 + CS2) * uy;
-    k[7] = RmP * (uy2 + CS2) * ux;
-    k[8] = -R * (ux2 * uy2 + CS2 * (ux2 + uy2)) + dP * (ux2 + CS2) * (uy2 + CS2);
-    float r[9];
-    central_to_raw(k, ux, uy, r);
-    raw_to_pops(r, a);
-}
-
-__device__ __forceinline__ void eq_scalar(float a[9], float s, float qx, float qy, float ux,
-                                          float uy) {
-    float k[9] = {s, qx, qy, CS2 * s, CS2 * s, 0.0f, 0.0f, 0.0f, CS2 * CS2 * s};
-    float r[9];
-    central_to_raw(k, ux, uy, r);
-    raw_to_pops(r, a);
-}
-
-// 3x3 neighbourhood of a field plane on the extended (periodic / mirrored)
-// grid; ysign = -1 flips the sign of mirrored ghost rows (y component of n).
-__device__ __forceinline__ void load3x3(const float* __restrict__ F, const KParams& p, int i, int j,
-                                        float v[3][3], bool odd_under_mirror = false) {
-    const int im = wrap_i(i - 1, p.nx), ip = wrap_i(i + 1, p.nx);
-#pragma unroll
-    for (int dy = -1; dy <= 1; ++dy) {
-        const int jj = j + dy;
-        const int64_t r = (int64_t)ext_row(jj, p.ny, p.walls) * p.pitch;
-        const float s = odd_under_mirror ? mirror_sign(jj, p.ny, p.walls) : 1.0f;
-        v[dy + 1][0] = s * F[r + im];
-        v[dy + 1][1] = s * F[r + i];
-        v[dy + 1][2] = s * F[r + ip];
-    }
-}
-
-__device__ __forceinline__ void load3x3_fx(const float* __restrict__ F, const KParams& p, int i,
-                                           int j, int v[3][3]) {
-    const int im = wrap_i(i - 1, p.nx), ip = wrap_i(i + 1, p.nx);
-#pragma unroll
-    for (int dy = -1; dy <= 1; ++dy) {
-        const int64_t r = (int64_t)ext_row(j + dy, p.ny, p.walls) * p.pitch;
-        v[dy + 1][0] = __float_as_int(F[r + im]);
-        v[dy + 1][1] = __float_as_int(F[r + i]);
-        v[dy + 1][2] = __float_as_int(F[r + ip]);
-    }
-}
-
-// Local values and stencil results one cell's collisions need.
-struct CellGeom {
-    int phi_fx;                  // phi in fixed point (exact interface factors)
-    float phi, c, sig, dps;      // zeroth moments, sigma(c), P* - P0
-    float nx, ny, gm;            // unit normal, |grad phi|
-    float kappa;                 // div n
-    float sgx, sgy;              // grad sigma
-    float pgx, pgy;              // grad (P* - P0)
-    float fgx, fgy;              // grad phi (for grad rho)
-};
-
-struct CellOut {
-    float ux, uy, dP;
-};
-
-// The three collisions of one cell at row j.  f and h enter as their first
-// moments (the zeroth moments are g.phi and g.c) and leave as deviation-form
-// outputs df, dh (q = 1..8); the flow populations gg are collided in place.
-template <bool COUPLED>
-__device__ __forceinline__ CellOut collide_cell(const KParams& p, const CellGeom& g, int j,
-                                                float ux_fixed, float uy_fixed, float fjx,
-                                                float fjy, float hjx, float hjy, float gg[9],
-                                                float df[9], float dh[9], bool do_collide) {
-    CellOut o;
-    // Eq. (theta) and the theta_c of Eq. (ISS)
-    float theta, theta_c;
-    interface_coeffs(p, g.phi_fx, g.c, theta, theta_c);
-    if (COUPLED) {
-        // surface-tension force, Eq. (Fs)
-        const float g2 = g.gm * g.gm;
-        const float nds = g.nx * g.sgx + g.ny * g.sgy;
-        const float Fsx = p.N_sigma * g2 * (-g.sig * g.kappa * g.nx + (g.sgx - g.nx * nds));
-        const float Fsy = p.N_sigma * g2 * (-g.sig * g.kappa * g.ny + (g.sgy - g.ny * nds));
-        const float Ftx = Fsx + p.fext_x, Fty = Fsy + p.fext_y;
-        const float rho = p.rho_uniform ? p.rho_a : lerp_phase(p, g.phi, p.rho_a, p.rho_b);
-        const float jx = (gg[1] - gg[3]) + (gg[5] - gg[6]) - (gg[7] - gg[8]);
-        const float jy = (gg[2] - gg[4]) + (gg[5] + gg[6]) - (gg[7] + gg[8]);
-        // cs2 rho u = sum e g + cs2 F_t / 2  (App. D).  The division uses the
-        // same rounded rho cs2 as the equilibrium, so j -> u -> rho cs2 u does
-        // not drift by the rounding of 1/3 every step.
-        const float R = rho * CS2;
-        o.ux = (jx + 0.5f * CS2 * Ftx) / R;
-        o.uy = (jy + 0.5f * CS2 * Fty) / R;
-        // F_p = -grad psi with psi = P* - rho cs2
-        float Fpx = -g.pgx, Fpy = -g.pgy;
-        if (!p.rho_uniform) {
-            const float drho = (p.rho_a - p.rho_b) * p.inv_dphi;
-            Fpx += CS2 * drho * g.fgx;
-            Fpy += CS2 * drho * g.fgy;
-        }
-        const float G = Fpx * o.ux + Fpy * o.uy;
-        o.dP = g.dps + 0.5f * G;  // P = sum g + sigma_00 / 2
-        if (do_collide) {
-            FlowMacro m;
-            m.ux = o.ux;
-            m.uy = o.uy;
-            m.rho = rho;
-            m.dPs = g.dps;
-            m.dP = o.dP;
-            m.Ftx = Ftx;
-            m.Fty = Fty;
-            m.Fpx = Fpx;
-            m.Fpy = Fpy;
-            m.w_nu = p.nu_uniform ? p.w_nu : rate_from_coeff(lerp_phase(p, g.phi, p.nu_a, p.nu_b));
-            collide_flow(gg, m, p.w_zeta);
-            wall_correct_flow(gg, p, j, rho);
-        }
-    } else {
-        o.ux = ux_fixed;
-        o.uy = uy_fixed;
-        o.dP = 0.0f;
-    }
-    if (do_collide) {
-        collide_scalar_dev(g.phi, fjx, fjy, p.M_phi * theta * g.nx, p.M_phi * theta * g.ny,
-                           p.w_kappa, o.ux, o.uy, df);
-        collide_scalar_dev(g.c, hjx, hjy, p.D_s * theta_c * g.nx, p.D_s * theta_c * g.ny,
-                           p.w_chi, o.ux, o.uy, dh);
-    }
-    return o;
-}
-
-// Store a deviation-form lattice: plane 0 <- S (fixed point), planes 1..8 <- d.
-__device__ __forceinline__ void store_dev(float* __restrict__ base, const KParams& p, int64_t idx,
-                                          int s_fx, const float d[9]) {
-    base[idx] = __int_as_float(s_fx);
-#pragma unroll
-    for (int q = 1; q < 9; ++q) base[q * p.plane + idx] = d[q];
-}
-
-__device__ __forceinline__ void store9(float* __restrict__ base, const KParams& p, int64_t idx,
-                                       const float a[9]) {
-#pragma unroll
-    for (int q = 0; q < 9; ++q) base[q * p.plane + idx] = a[q];
-}
 
 // ---------------------------------------------------------------------------
 // three-kernel chain
@@ -280,9 +112,9 @@ __global__ void k_collide(KParams p, const float* __restrict__ src, float* __res
         ufy = F[FP_UY * p.plane + idx];
     }
     collide_cell<COUPLED>(p, g, j, ufx, ufy, mf.jx, mf.jy, mh.jx, mh.jy, gg, df, dh, true);
-    store_dev(dst, p, idx, f_fx, df);
-    store_dev(dst + 9 * p.plane, p, idx, h_fx, dh);
-    if (COUPLED) store9(dst + 18 * p.plane, p, idx, gg);
+    store_dev(dst, p, idx, i, f_fx, df);
+    store_dev(dst + 9 * p.plane, p, idx, i, h_fx, dh);
+    if (COUPLED) store9(dst + 18 * p.plane, p, idx, i, gg);
 }
 
 template <bool COUPLED>
@@ -306,8 +138,8 @@ __global__ void k_macro_out(KParams p, const float* __restrict__ src, const floa
     }
     CellOut r = collide_cell<COUPLED>(p, g, j, ufx, ufy, 0.0f, 0.0f, 0.0f, 0.0f, gg, nullptr,
                                       nullptr, false);
-    if (ophi) ophi[o] = (double)g.phi_fx / (double)p.fx_scale[0];
-    if (oc) oc[o] = (double)__float_as_int(F[FP_C * p.plane + idx]) / (double)p.fx_scale[1];
+    if (ophi) ophi[o] = fx_to_double(g.phi_fx, p.fx_scale[0]);
+    if (oc) oc[o] = fx_to_double(__float_as_int(F[FP_C * p.plane + idx]), p.fx_scale[1]);
     if (oux) oux[o] = r.ux;
     if (ouy) ouy[o] = r.uy;
     if (oP) oP[o] = COUPLED ? (double)p.P0 + (double)r.dP : 0.0;
@@ -480,9 +312,9 @@ __global__ void __launch_bounds__(128) k_fused_sweep(KParams p, const float* __r
                 ufy = F[FP_UY * p.plane + idx];
             }
             collide_cell<COUPLED>(p, g, jc, ufx, ufy, fjx, fjy, hjx, hjy, gg, df, dh, true);
-            store_dev(dst, p, idx, g.phi_fx, df);
-            store_dev(dst + 9 * p.plane, p, idx, h_fx, dh);
-            if (COUPLED) store9(dst + 18 * p.plane, p, idx, gg);
+            store_dev(dst, p, idx, i, g.phi_fx, df);
+            store_dev(dst + 9 * p.plane, p, idx, i, h_fx, dh);
+            if (COUPLED) store9(dst + 18 * p.plane, p, idx, i, gg);
         }
     }
 }
@@ -502,8 +334,8 @@ __global__ void k_init_fields(KParams p, const double* __restrict__ phi,
     const int64_t o = (int64_t)j * p.nx + i;
     const float fphi = (float)phi[o];
     const float fc = (float)c[o];
-    F[FP_PHI * p.plane + idx] = __int_as_float(__double2int_rn(phi[o] * (double)p.fx_scale[0]));
-    F[FP_C * p.plane + idx] = __int_as_float(__double2int_rn(c[o] * (double)p.fx_scale[1]));
+    F[FP_PHI * p.plane + idx] = __int_as_float(fx_from_double(phi[o], p.fx_scale[0]));
+    F[FP_C * p.plane + idx] = __int_as_float(fx_from_double(c[o], p.fx_scale[1]));
     F[FP_SIG * p.plane + idx] = sigma_of_c(p, fc);
     F[FP_UX * p.plane + idx] = (float)ux[o];
     F[FP_UY * p.plane + idx] = (float)uy[o];
@@ -532,13 +364,13 @@ __global__ void k_init_pre(KParams p, const float* __restrict__ F, float* __rest
     interface_coeffs(p, phi_fx, c, theta, theta_c);
     float a[9];
     eq_scalar(a, phi, p.M_phi * theta * nx, p.M_phi * theta * ny, ux, uy);
-    store9(pre, p, idx, a);
+    store9_plain(pre, p, idx, a);
     eq_scalar(a, c, p.D_s * theta_c * nx, p.D_s * theta_c * ny, ux, uy);
-    store9(pre + 9 * p.plane, p, idx, a);
+    store9_plain(pre + 9 * p.plane, p, idx, a);
     if (COUPLED) {
         const float rho = p.rho_uniform ? p.rho_a : lerp_phase(p, phi, p.rho_a, p.rho_b);
         eq_flow_shifted(a, F[FP_DPS * p.plane + idx], rho, ux, uy);
-        store9(pre + 18 * p.plane, p, idx, a);
+        store9_plain(pre + 18 * p.plane, p, idx, a);
     }
 }
 
@@ -571,15 +403,14 @@ __global__ void k_unstream(KParams p, int nlat, const float* __restrict__ pre,
             double S = 0.0;
 #pragma unroll
             for (int q = 0; q < 9; ++q) S += (double)u[q];
-            const int S_fx = __double2int_rn(S * (double)p.fx_scale[l]);
-            const double Sr = (double)S_fx / (double)p.fx_scale[l];
-            dl[idx] = __int_as_float(S_fx);
+            const int S_fx = fx_from_double(S, p.fx_scale[l]);
+            const double Sr = fx_to_double(S_fx, p.fx_scale[l]);
+            float d[9];
 #pragma unroll
-            for (int q = 1; q < 9; ++q)
-                dl[q * p.plane + idx] = (float)((double)u[q] - (double)wq(q) * Sr);
+            for (int q = 1; q < 9; ++q) d[q] = (float)((double)u[q] - (double)wq(q) * Sr);
+            store_dev(dl, p, idx, i, S_fx, d);
         } else {
-#pragma unroll
-            for (int q = 0; q < 9; ++q) dl[q * p.plane + idx] = u[q];
+            store9(dl, p, idx, i, u);
         }
     }
 }
@@ -597,7 +428,7 @@ __global__ void k_pull_pre(KParams p, int nlat, const float* __restrict__ src,
             pull9_dev<float>(src + (int64_t)l * 9 * p.plane, p, l, i, j, a);
         else
             pull9(src + (int64_t)l * 9 * p.plane, p, i, j, a);
-        store9(pre + (int64_t)l * 9 * p.plane, p, idx, a);
+        store9_plain(pre + (int64_t)l * 9 * p.plane, p, idx, a);
     }
 }
 

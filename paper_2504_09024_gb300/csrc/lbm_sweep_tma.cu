@@ -1,0 +1,388 @@
+// Fused step with bulk-tensor (TMA) staging of the populations.
+//
+// Same sweep as k_fused_sweep (a block owns a strip of columns and walks down
+// a segment of rows, forming phi, c, sigma, P* one row ahead in shared-memory
+// rings, the unit normal one row behind and colliding two rows behind), but
+// the raw rows are brought in by one 3-D TMA box per row
+// ({columns, 1 row, all planes}) issued by one thread, TMA_STAGES - 3 rows
+// ahead of use, and completing on an mbarrier.  Every pull then reads shared
+// memory; every population byte leaves HBM once per strip.  Periodic x needs
+// no wrap logic: the boxes include the ghost columns the writers maintain.
+// Walls: rows beyond a wall are never loaded; their ring entries are mirror
+// copies of rows already formed (row -1-k is row k, row ny+k is ny-1-k).
+#include <cstdio>
+
+#include <cudaTypedefs.h>
+
+#include "lbm_cell.cuh"
+#include "lbm_tma.cuh"
+
+namespace lbm {
+
+namespace {
+
+constexpr int TMA_STAGES = 5;  // staged raw rows: the three a row's pull reads, two ahead
+constexpr int T_RING = 6;    // rows of phi, c, sigma, P* kept (and mirror copies)
+constexpr int T_NRING = 3;   // rows of n, |grad phi|
+constexpr int T_PRING = 3;   // rows of interior cells waiting for their collision
+constexpr int T_PSLOT = 15;  // f (jx, jy), h (S, jx, jy), g (9 populations)
+
+template <int BX, bool COUPLED>
+struct TmaLayout {
+    static constexpr int NL = COUPLED ? 27 : 18;       // planes per box
+    static constexpr int W = BX + 4;                   // staged columns x0-4 .. x0+BX-1
+    static constexpr int SLOT = (NL * W + 31) / 32 * 32;  // floats per staged row (128-B multiple)
+    static constexpr size_t bytes =
+        128 /* barriers */ + sizeof(float) * ((size_t)TMA_STAGES * SLOT + (size_t)T_RING * 4 * BX +
+                                              (size_t)T_NRING * 3 * BX +
+                                              (size_t)T_PRING * T_PSLOT * BX) +
+        128 /* alignment slack */;
+};
+
+__device__ __forceinline__ int rmod(int a, int m) { return ((a % m) + m) % m; }
+
+}  // namespace
+
+template <int BX, bool COUPLED>
+__global__ void __launch_bounds__(BX) k_sweep_tma(const __grid_constant__ CUtensorMap tmap,
+                                                  KParams p, float* __restrict__ dst,
+                                                  const float* __restrict__ F, int seg,
+                                                  int* __restrict__ err) {
+    using L = TmaLayout<BX, COUPLED>;
+    constexpr int NL = L::NL, W = L::W, SLOT = L::SLOT, TX = BX - 4;
+    extern __shared__ unsigned char smem_raw[];
+    const uintptr_t base = (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~(uintptr_t)127;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(base);
+    float* raw = reinterpret_cast<float*>(base + 128);
+    int* s_phi = reinterpret_cast<int*>(raw + TMA_STAGES * SLOT);  // [T_RING][BX] fixed point
+    float* s_c = reinterpret_cast<float*>(s_phi + T_RING * BX);
+    float* s_sig = s_c + T_RING * BX;
+    float* s_dps = s_sig + T_RING * BX;
+    float* s_nx = s_dps + T_RING * BX;  // [T_NRING][BX]
+    float* s_ny = s_nx + T_NRING * BX;
+    float* s_gm = s_ny + T_NRING * BX;
+    float* s_pop = s_gm + T_NRING * BX;  // [T_PRING][T_PSLOT][BX]
+
+    const int t = threadIdx.x;
+    const int x0 = blockIdx.x * TX;
+    const int xend = min(x0 + TX, p.nx);
+    const int y0 = blockIdx.y * seg;
+    const int y1 = min(y0 + seg, p.ny);
+    const int col = x0 - 2 + t;
+    int role = 0;
+    if (col >= x0 && col < xend) role = 3;
+    else if (col == x0 - 1 || col == xend) role = 2;
+    else if (col == x0 - 2 || col == xend + 1) role = 1;
+    const int i = wrap_i(col, p.nx);
+    const int cs = t + 2;  // this column's index in a staged row (staged column 0 is x0 - 4)
+
+    // rows swept: phi for y0-2 .. y1+1; beyond walls only mirror copies
+    const int rs = p.walls ? max(y0 - 2, 0) : y0 - 2;
+    const int re = p.walls ? min(y1 + 1, p.ny + 1) : y1 + 1;
+    const int last_phys = p.walls ? min(re, p.ny - 1) : re;
+    // staged raw rows: rs-1 .. last_phys+1, counter k = row - (rs - 1)
+    const int nraw = last_phys - rs + 3;
+
+    if (t == 0) {
+        for (int k = 0; k <= TMA_STAGES; ++k) mbar_init(&bars[k], 1);  // [TMA_STAGES]: test hook
+        fence_barrier_init();
+    }
+    __syncthreads();
+
+    auto issue = [&](int k) {  // thread 0: stage raw row rs - 1 + k
+        if (k >= nraw) return;
+        const int row = rs - 1 + k;
+        const int y = p.walls ? row : wrap_i(row, p.ny);  // rows beyond walls read fill values
+        const int slot = k % TMA_STAGES;
+        mbar_arrive_expect_tx(&bars[slot], (uint32_t)(NL * W * sizeof(float)));
+        // padded x coordinate of column x0 - 4 is x0 (XGHOST == 4)
+        tma_load_3d(raw + slot * SLOT, &tmap, x0 - 4 + XGHOST, y, 0, &bars[slot]);
+    };
+    auto staged = [&](int row) { return raw + ((row - rs + 1) % TMA_STAGES) * SLOT; };
+    auto wait_row = [&](int row) -> bool {
+        const int k = row - rs + 1;
+        return mbar_wait_bounded(&bars[k % TMA_STAGES], (uint32_t)((k / TMA_STAGES) & 1));
+    };
+
+    int issued = 0;  // staged rows issued so far (thread 0)
+    if (t == 0) {
+        fence_proxy_async();
+        for (int k = 0; k < TMA_STAGES; ++k) issue(k);
+        issued = min(TMA_STAGES, nraw);
+    }
+
+    bool failed = false;
+    if (p.stall_test) {
+        // failure-path test: wait on a barrier that no copy completes
+        const bool ok = mbar_wait_bounded(&bars[TMA_STAGES], 0, 4096);
+        failed = !__syncthreads_and(ok);
+    }
+    for (int r = rs; r <= re && !failed; ++r) {
+        const bool phys = !p.walls || r < p.ny;
+        const int slot = rmod(r, T_RING);
+        // ---------------- A: moments of row r ----------------
+        if (phys) {
+            bool ok = true;
+            if (r == rs) ok = wait_row(r - 1) && wait_row(r);
+            ok = ok && wait_row(r + 1);
+            if (!__syncthreads_and(ok)) {
+                failed = true;
+                break;
+            }
+            if (role > 0) {
+                const int jj = p.walls ? r : wrap_i(r, p.ny);
+                const bool bot = p.walls && jj == 0, top = p.walls && jj == p.ny - 1;
+                const float* Rm = staged(r - 1);
+                const float* R0 = staged(r);
+                const float* Rp = staged(r + 1);
+                const bool keep = role == 3 && r >= y0 && r < y1;
+                float* pp = s_pop + rmod(r, T_PRING) * T_PSLOT * BX;
+                ScalarMoments m =
+                    pull_scalar_rows(Rm, R0, Rp, W, cs - 1, cs, cs + 1, bot, top, p.fx_inv[0]);
+                s_phi[slot * BX + t] = fx_add(m.s0, m.inc, p.fx_scale[0]);
+                if (keep) {
+                    pp[0 * BX + t] = m.jx;
+                    pp[1 * BX + t] = m.jy;
+                }
+                if (role >= 2) {
+                    m = pull_scalar_rows(Rm + 9 * W, R0 + 9 * W, Rp + 9 * W, W, cs - 1, cs, cs + 1,
+                                         bot, top, p.fx_inv[1]);
+                    const int c_fx = fx_add(m.s0, m.inc, p.fx_scale[1]);
+                    const float c = (float)c_fx * p.fx_inv[1];
+                    s_c[slot * BX + t] = c;
+                    s_sig[slot * BX + t] = sigma_of_c(p, c);
+                    if (keep) {
+                        pp[2 * BX + t] = __int_as_float(c_fx);
+                        pp[3 * BX + t] = m.jx;
+                        pp[4 * BX + t] = m.jy;
+                    }
+                    if (COUPLED) {
+                        float a[9];
+                        pull9_rows(Rm + 18 * W, R0 + 18 * W, Rp + 18 * W, W, cs - 1, cs, cs + 1,
+                                   bot, top, a);
+                        s_dps[slot * BX + t] = sum9(a);
+                        if (keep) {
+#pragma unroll
+                            for (int q = 0; q < 9; ++q) pp[(6 + q) * BX + t] = a[q];
+                        }
+                    }
+                }
+                // mirror rows below the bottom wall, formed once rows 0 and 1 exist
+                if (p.walls && r == 1) {
+                    for (int src = 0; src <= 1; ++src) {
+                        const int g = -1 - src;
+                        if (g < y0 - 2) continue;
+                        const int gs = rmod(g, T_RING), ss = rmod(src, T_RING);
+                        s_phi[gs * BX + t] = s_phi[ss * BX + t];
+                        if (role >= 2) {
+                            s_c[gs * BX + t] = s_c[ss * BX + t];
+                            s_sig[gs * BX + t] = s_sig[ss * BX + t];
+                            s_dps[gs * BX + t] = s_dps[ss * BX + t];
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+            // the staged row r-1 is consumed: reuse its slot for row r-1+TMA_STAGES
+            if (t == 0) {
+                fence_proxy_async();
+                issue(r - rs + TMA_STAGES);
+                issued = min(r - rs + TMA_STAGES + 1, nraw);
+            }
+        } else {
+            // mirror row above the top wall
+            if (role > 0) {
+                const int ss = rmod(2 * p.ny - 1 - r, T_RING);
+                s_phi[slot * BX + t] = s_phi[ss * BX + t];
+                if (role >= 2) {
+                    s_c[slot * BX + t] = s_c[ss * BX + t];
+                    s_sig[slot * BX + t] = s_sig[ss * BX + t];
+                    s_dps[slot * BX + t] = s_dps[ss * BX + t];
+                }
+            }
+            __syncthreads();
+        }
+        // ---------------- B: unit normal one row behind ----------------
+        for (int pass = 0; pass < 2; ++pass) {
+            int rn = r - 1;
+            if (pass == 1) {
+                // with a bottom wall, n(-1) needs the mirror of row 1, available at r = 1
+                if (!(p.walls && r == 1 && y0 == 0)) break;
+                rn = -1;
+            } else if (p.walls && rn == -1) {
+                continue;
+            }
+            if (role >= 2 && rn >= y0 - 1 && rn <= y1) {
+                const int sm1 = rmod(rn - 1, T_RING), s0 = rmod(rn, T_RING), sp1 = rmod(rn + 1, T_RING);
+                int v[3][3];
+                v[0][0] = s_phi[sm1 * BX + t - 1]; v[0][1] = s_phi[sm1 * BX + t]; v[0][2] = s_phi[sm1 * BX + t + 1];
+                v[1][0] = s_phi[s0 * BX + t - 1];  v[1][1] = s_phi[s0 * BX + t];  v[1][2] = s_phi[s0 * BX + t + 1];
+                v[2][0] = s_phi[sp1 * BX + t - 1]; v[2][1] = s_phi[sp1 * BX + t]; v[2][2] = s_phi[sp1 * BX + t + 1];
+                float gx, gy, nx, ny, gm;
+                iso_grad_fx(v, p.fx_inv[0], gx, gy);
+                unit_normal(gx, gy, nx, ny, gm);
+                const int ns = rmod(rn, T_NRING);
+                s_nx[ns * BX + t] = nx;
+                s_ny[ns * BX + t] = ny;
+                s_gm[ns * BX + t] = gm;
+            }
+        }
+        __syncthreads();
+        // ---------------- C: collide row r-2 ----------------
+        const int jc = r - 2;
+        if (role == 3 && jc >= y0 && jc < y1) {
+            const int c0 = rmod(jc, T_RING);
+            const int cr[3] = {rmod(jc - 1, T_RING), c0, rmod(jc + 1, T_RING)};
+            const int nr[3] = {rmod(jc - 1, T_NRING), rmod(jc, T_NRING), rmod(jc + 1, T_NRING)};
+            CellGeom g;
+            g.phi_fx = s_phi[c0 * BX + t];
+            g.phi = (float)g.phi_fx * p.fx_inv[0];
+            g.c = s_c[c0 * BX + t];
+            g.sig = s_sig[c0 * BX + t];
+            g.nx = s_nx[nr[1] * BX + t];
+            g.ny = s_ny[nr[1] * BX + t];
+            g.gm = s_gm[nr[1] * BX + t];
+            if (COUPLED) {
+                g.dps = s_dps[c0 * BX + t];
+                float vx[3][3], vy[3][3], v[3][3];
+#pragma unroll
+                for (int d = 0; d < 3; ++d)
+#pragma unroll
+                    for (int e = 0; e < 3; ++e) {
+                        vx[d][e] = s_nx[nr[d] * BX + t - 1 + e];
+                        vy[d][e] = s_ny[nr[d] * BX + t - 1 + e];
+                    }
+                g.kappa = iso_div(vx, vy);
+#pragma unroll
+                for (int d = 0; d < 3; ++d)
+#pragma unroll
+                    for (int e = 0; e < 3; ++e) v[d][e] = s_sig[cr[d] * BX + t - 1 + e];
+                iso_grad(v, g.sgx, g.sgy);
+#pragma unroll
+                for (int d = 0; d < 3; ++d)
+#pragma unroll
+                    for (int e = 0; e < 3; ++e) v[d][e] = s_dps[cr[d] * BX + t - 1 + e];
+                iso_grad(v, g.pgx, g.pgy);
+                if (!p.rho_uniform) {
+                    int vi[3][3];
+#pragma unroll
+                    for (int d = 0; d < 3; ++d)
+#pragma unroll
+                        for (int e = 0; e < 3; ++e) vi[d][e] = s_phi[cr[d] * BX + t - 1 + e];
+                    iso_grad_fx(vi, p.fx_inv[0], g.fgx, g.fgy);
+                } else {
+                    g.fgx = g.fgy = 0.0f;
+                }
+            } else {
+                g.dps = 0.0f;
+                g.kappa = g.sgx = g.sgy = g.pgx = g.pgy = g.fgx = g.fgy = 0.0f;
+            }
+            const float* pp = s_pop + rmod(jc, T_PRING) * T_PSLOT * BX;
+            const float fjx = pp[0 * BX + t], fjy = pp[1 * BX + t];
+            const int h_fx = __float_as_int(pp[2 * BX + t]);
+            const float hjx = pp[3 * BX + t], hjy = pp[4 * BX + t];
+            float gg[9], df[9], dh[9];
+#pragma unroll
+            for (int q = 0; q < 9; ++q) gg[q] = COUPLED ? pp[(6 + q) * BX + t] : 0.0f;
+            const int64_t idx = (int64_t)jc * p.pitch + i;
+            float ufx = 0.0f, ufy = 0.0f;
+            if (!COUPLED) {
+                ufx = F[FP_UX * p.plane + idx];
+                ufy = F[FP_UY * p.plane + idx];
+            }
+            collide_cell<COUPLED>(p, g, jc, ufx, ufy, fjx, fjy, hjx, hjy, gg, df, dh, true);
+            store_dev(dst, p, idx, i, g.phi_fx, df);
+            store_dev(dst + 9 * p.plane, p, idx, i, h_fx, dh);
+            if (COUPLED) store9(dst + 18 * p.plane, p, idx, i, gg);
+        }
+    }
+    if (failed) {
+        // a staged row never landed: report, then let copies still in flight finish
+        if (t == 0) {
+            atomicExch(err, 1);
+            for (int k = max(0, issued - TMA_STAGES); k < issued; ++k)
+                mbar_wait_bounded(&bars[k % TMA_STAGES], (uint32_t)((k / TMA_STAGES) & 1));
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+
+namespace {
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* ptr = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000,
+                                             cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
+    }
+    return fn;
+}
+
+template <int BX, bool COUPLED>
+void set_attr() {
+    cudaFuncSetAttribute(k_sweep_tma<BX, COUPLED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)TmaLayout<BX, COUPLED>::bytes);
+}
+
+}  // namespace
+
+bool tma_available() { return encode_fn() != nullptr; }
+
+// Tensor map over one population buffer: dims {pitch, ny, planes}, box
+// {bx + 4, 1, planes}.
+bool make_tensor_map(CUtensorMap* map, float* alloc, const KParams& p, int nplanes, int bx) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+    if (!enc) return false;
+    cuuint64_t dims[3] = {(cuuint64_t)p.pitch, (cuuint64_t)p.ny, (cuuint64_t)nplanes};
+    cuuint64_t strides[2] = {(cuuint64_t)p.pitch * sizeof(float),
+                             (cuuint64_t)p.plane * sizeof(float)};
+    cuuint32_t box[3] = {(cuuint32_t)(bx + 4), 1u, (cuuint32_t)nplanes};
+    cuuint32_t estr[3] = {1u, 1u, 1u};
+    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, alloc, dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+size_t tma_smem_bytes(int bx, bool coupled) {
+    if (bx == 128) return coupled ? TmaLayout<128, true>::bytes : TmaLayout<128, false>::bytes;
+    if (bx == 64) return coupled ? TmaLayout<64, true>::bytes : TmaLayout<64, false>::bytes;
+    return 0;
+}
+
+cudaError_t configure_tma_smem() {
+    set_attr<128, true>();
+    set_attr<128, false>();
+    set_attr<64, true>();
+    set_attr<64, false>();
+    return cudaGetLastError();
+}
+
+void launch_step_tma(const KParams& p, const DevState& s, int src, const FusedShape& sh,
+                     const CUtensorMap* maps, int* err, cudaStream_t st) {
+    const int tx = sh.bx - 4;
+    dim3 grid((p.nx + tx - 1) / tx, (p.ny + sh.seg - 1) / sh.seg);
+    const size_t smem = tma_smem_bytes(sh.bx, p.coupled);
+    float* dst = s.pop[1 - src];
+    if (sh.bx == 128) {
+        if (p.coupled)
+            k_sweep_tma<128, true><<<grid, 128, smem, st>>>(maps[src], p, dst, s.fields, sh.seg, err);
+        else
+            k_sweep_tma<128, false><<<grid, 128, smem, st>>>(maps[src], p, dst, s.fields, sh.seg, err);
+    } else {
+        if (p.coupled)
+            k_sweep_tma<64, true><<<grid, 64, smem, st>>>(maps[src], p, dst, s.fields, sh.seg, err);
+        else
+            k_sweep_tma<64, false><<<grid, 64, smem, st>>>(maps[src], p, dst, s.fields, sh.seg, err);
+    }
+}
+
+}  // namespace lbm

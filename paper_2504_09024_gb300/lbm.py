@@ -33,7 +33,7 @@ LBM_ERR_NOMEM = -9
 
 LBM_F32, LBM_F16S, LBM_BF16S = 1, 2, 3
 LBM_COUPLED, LBM_FIXED_U = 0, 1
-LBM_KERNEL_AUTO, LBM_KERNEL_SPLIT, LBM_KERNEL_FUSED = 0, 1, 2
+LBM_KERNEL_AUTO, LBM_KERNEL_SPLIT, LBM_KERNEL_FUSED, LBM_KERNEL_TMA = 0, 1, 2, 3
 
 
 class lbm_params(ctypes.Structure):
@@ -84,6 +84,7 @@ SIGNATURES = {
                                             ctypes.POINTER(ctypes.c_int32)]),
     "lbm_save_state": (ctypes.c_int, [_VP, ctypes.c_char_p]),
     "lbm_load_state": (ctypes.c_int, [_VP, ctypes.c_char_p]),
+    "lbm_debug_stall_next_step": (ctypes.c_int, [_VP]),
     "lbm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
 }
 
@@ -229,6 +230,10 @@ def lbm_save_state(ctx, path: str):
 
 def lbm_load_state(ctx, path: str):
     _check(load().lbm_load_state(ctx, path.encode()), "lbm_load_state")
+
+
+def lbm_debug_stall_next_step(ctx):
+    _check(load().lbm_debug_stall_next_step(ctx), "lbm_debug_stall_next_step")
 
 
 def lbm_strerror(code: int) -> str:
