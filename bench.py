@@ -224,7 +224,7 @@ def run_ours(args, rank, world, local_rank):
     nx, ny = case.phys.nx, case.phys.ny
     ncell = nx * ny
     dtype_code = {"f32": lbm.LBM_F32, "f16s": lbm.LBM_F16S, "bf16s": lbm.LBM_BF16S}[args.dtype]
-    kern = {"auto": lbm.LBM_KERNEL_AUTO, "fused": lbm.LBM_KERNEL_FUSED,
+    kern = {"auto": lbm.LBM_KERNEL_AUTO, "tma": lbm.LBM_KERNEL_TMA, "fused": lbm.LBM_KERNEL_FUSED,
             "split": lbm.LBM_KERNEL_SPLIT}[args.kernel]
     stream = torch.cuda.Stream()
     sim = lbm.Sim(case.phys, dtype=dtype_code, kernel=kern, stream=stream.cuda_stream)
@@ -282,7 +282,8 @@ def run_ours(args, rank, world, local_rank):
     peak, peak_kind = peaks()
     bpc = BYTES_PER_CELL[args.dtype]
     achieved = bpc * ncell / (ms_step * 1e-3) / 1e9
-    kname = "k_fused_sweep" if lbm.lbm_kernel_in_use(sim.ctx) == lbm.LBM_KERNEL_FUSED else "k_collide"
+    kname = {lbm.LBM_KERNEL_TMA: "k_sweep_tma", lbm.LBM_KERNEL_FUSED: "k_fused_sweep",
+             lbm.LBM_KERNEL_SPLIT: "k_collide"}[lbm.lbm_kernel_in_use(sim.ctx)]
     tr = traffic_record(kname)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -323,7 +324,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="2048x1024")
     ap.add_argument("--dtype", choices=["f32", "f16s", "bf16s"], default="f32")
-    ap.add_argument("--kernel", choices=["auto", "fused", "split"], default="auto")
+    ap.add_argument("--kernel", choices=["auto", "tma", "fused", "split"], default="auto")
     ap.add_argument("--tile-x", type=int, default=0)
     ap.add_argument("--seg-y", type=int, default=0)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
