@@ -205,6 +205,38 @@ int lbm_load_state(lbm_ctx *ctx, const char *path);
  * Errors: INVALID_ARG, UNSUPPORTED (other kernels). */
 int lbm_debug_stall_next_step(lbm_ctx *ctx);
 
+/* ------------------------------------------------------------------------
+ * Field statistics without allocation.  The paper has no counterpart: this
+ * entry point serves callers that cannot allocate device memory where they
+ * need the statistics (a memory pool with a hard cap, a framework that
+ * forbids allocations inside its step loop).  It computes, in FP64, the same
+ * reductions as lbm_diagnostics over caller-owned device fields and allocates
+ * nothing: its scratch is a file-scope device array of
+ * LBM_NOALLOC_MAX_BLOCKS x 12 doubles (96 KiB) that every GPU loading this
+ * library holds until the process exits.
+ *
+ * phi, c, ux, uy: device float64 [ny][nx] fields (inputs, not modified).
+ * walls_y: 0 periodic y (circular-mean centroid), 1 walls (plain mean).
+ * beta, c_max: Langmuir parameters for the sigma < 0 count (Eq. EOS).
+ * result: device array of LBM_FIELD_STATS_LEN doubles, written in full:
+ *   [0] sum phi  [1] sum c  [2] xc  [3] yc  [4] non-finite cells
+ *   [5] cells with sigma < 0  [6] max |u|  [7] Ixx  [8] Iyy  [9] Ixy
+ *   [10] L  [11] B  [12] D   (moments, L, B, D as in lbm_diag)
+ * stream: cudaStream_t to run on (NULL: the legacy default stream).
+ * Asynchronous on `stream`.  The first call on a device looks up the device
+ * address of the scratch array (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  Every call
+ * overwrites the scratch before reading it, so nothing needs clearing, but
+ * calls that overlap on the GPU share the array and race.
+ * Errors: INVALID_ARG (NULL pointer, nx or ny < 1, nx * ny >
+ * LBM_NOALLOC_MAX_CELLS, bad walls_y or c_max), CUDA. */
+#define LBM_FIELD_STATS_LEN 13
+#define LBM_NOALLOC_MAX_BLOCKS 1024
+#define LBM_NOALLOC_MAX_CELLS 1073741824
+int lbm_field_stats_noalloc(const double *phi, const double *c, const double *ux,
+                            const double *uy, int32_t nx, int32_t ny, int32_t walls_y,
+                            double beta, double c_max, double *result, void *stream);
+
 /* Static description of an error code. */
 const char *lbm_strerror(int code);
 

@@ -85,8 +85,13 @@ SIGNATURES = {
     "lbm_save_state": (ctypes.c_int, [_VP, ctypes.c_char_p]),
     "lbm_load_state": (ctypes.c_int, [_VP, ctypes.c_char_p]),
     "lbm_debug_stall_next_step": (ctypes.c_int, [_VP]),
+    "lbm_field_stats_noalloc": (ctypes.c_int, [_DP, _DP, _DP, _DP, ctypes.c_int32, ctypes.c_int32,
+                                               ctypes.c_int32, ctypes.c_double, ctypes.c_double,
+                                               _DP, _VP]),
     "lbm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
 }
+
+LBM_FIELD_STATS_LEN = 13
 
 _lib = None
 _lock = threading.Lock()
@@ -234,6 +239,14 @@ def lbm_load_state(ctx, path: str):
 
 def lbm_debug_stall_next_step(ctx):
     _check(load().lbm_debug_stall_next_step(ctx), "lbm_debug_stall_next_step")
+
+
+def lbm_field_stats_noalloc(phi, c, ux, uy, nx, ny, walls_y, beta, c_max, result, stream=None):
+    """FP64 field statistics of device fields into the device array `result`
+    (LBM_FIELD_STATS_LEN doubles) without any device allocation."""
+    _check(load().lbm_field_stats_noalloc(_addr(phi), _addr(c), _addr(ux), _addr(uy), int(nx),
+                                          int(ny), int(walls_y), float(beta), float(c_max),
+                                          _addr(result), stream), "lbm_field_stats_noalloc")
 
 
 def lbm_strerror(code: int) -> str:
