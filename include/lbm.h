@@ -206,6 +206,69 @@ int lbm_load_state(lbm_ctx *ctx, const char *path);
 int lbm_debug_stall_next_step(lbm_ctx *ctx);
 
 /* ------------------------------------------------------------------------
+ * Launch-shape autotuner.  Times every candidate (block width tile_x, rows
+ * per block seg_y) over `steps` steps of the live state (after 2 warm-up
+ * steps, CUDA events on the context's stream), restores the state, step count
+ * and buffer parity after each candidate, and keeps the fastest shape.
+ * Candidates: tile_x in {128, 64} (TMA kernel; 128 only for FUSED), seg_y in
+ * {8, 16, 32, 64, 128} plus the values that fill one and two waves of
+ * resident blocks.  Needs one extra device buffer the size of a population
+ * buffer while it runs.  Outputs (nullable): chosen shape and its time per
+ * step in milliseconds.  Synchronous.
+ * Errors: INVALID_ARG (steps < 1), UNSUPPORTED (split kernel), NOMEM, CUDA,
+ * TIMEOUT. */
+int lbm_autotune(lbm_ctx *ctx, int32_t steps, int32_t *tile_x, int32_t *seg_y,
+                 double *ms_per_step);
+
+/* ------------------------------------------------------------------------
+ * Batches (ensembles of independent runs, e.g. drops in shear at different
+ * grid sizes and parameters).  A batch owns one context per run; every
+ * batched step advances all runs by one persistent launch of the TMA sweep
+ * kernel that walks a list of tiles over all runs (larger runs first), and
+ * step loops are replayed from captured CUDA graphs.  Runs are independent:
+ * each follows Sec. 3 and App. C-D exactly as a single context does, and a
+ * batched step gives results identical to stepping each run's context on its
+ * own with the same launch shape.
+ */
+typedef struct lbm_batch lbm_batch;
+
+/* params: array of nruns parameter sets (grid, physics, walls may differ;
+ * mode must be the same for all; kernel must be AUTO or TMA).  stream:
+ * cudaStream_t shared by the batch and its runs (NULL: a private stream).
+ * Errors: INVALID_ARG, RATE, UNSUPPORTED (no TMA support, kernel choice),
+ * NOMEM, CUDA. */
+int lbm_batch_create(const lbm_params *params, int32_t nruns, void *stream, lbm_batch **out);
+void lbm_batch_destroy(lbm_batch *b);
+int32_t lbm_batch_size(const lbm_batch *b);
+
+/* Context of run `run` (owned by the batch; NULL if out of range).  Use it
+ * with lbm_init_fields, lbm_get_fields, lbm_diagnostics, lbm_save_state and
+ * the other single-run calls; stepping it alone is allowed (the next batched
+ * step picks up its buffer parity). */
+lbm_ctx *lbm_batch_run(lbm_batch *b, int32_t run);
+
+/* Advance every run by nsteps (asynchronous on the batch stream). */
+int lbm_batch_step(lbm_batch *b, int64_t nsteps);
+
+/* Wait for the batch stream; reports a pending CUDA error or an expired
+ * bounded wait (LBM_ERR_TIMEOUT) of a batched step. */
+int lbm_batch_synchronize(lbm_batch *b);
+
+/* Block width (64 or 128 threads; the block owns tile_x - 4 columns) and
+ * rows per tile (>= 4) of the batched kernel; 0 keeps the current value.
+ * The getter also reports the persistent grid size and the number of tiles.
+ * Errors: INVALID_ARG, UNSUPPORTED. */
+int lbm_batch_set_launch_shape(lbm_batch *b, int32_t tile_x, int32_t seg_y);
+int lbm_batch_get_launch_shape(const lbm_batch *b, int32_t *tile_x, int32_t *seg_y,
+                               int32_t *blocks, int32_t *tiles);
+
+/* Autotuner of the batched launch shape: tile_x in {128, 64} x seg_y in
+ * {16, 24, 32, 48, 64, 96, 128}, timed and restored as in lbm_autotune
+ * (one snapshot buffer per run while it runs).  Synchronous. */
+int lbm_batch_autotune(lbm_batch *b, int32_t steps, int32_t *tile_x, int32_t *seg_y,
+                       double *ms_per_step);
+
+/* ------------------------------------------------------------------------
  * Field statistics without allocation.  The paper has no counterpart: this
  * entry point serves callers that cannot allocate device memory where they
  * need the statistics (a memory pool with a hard cap, a framework that

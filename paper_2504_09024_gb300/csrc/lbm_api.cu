@@ -2,6 +2,7 @@
 // parameter validation, host <-> device staging, CUDA-graph replay of long
 // step loops, diagnostics and checkpoints.  All arithmetic of the method runs
 // in the kernels of lbm_kernels.cu.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -616,6 +617,511 @@ int lbm_load_state(lbm_ctx* ctx, const char* path) {
     std::free(host);
     if (e != cudaSuccess) return cuda_fail(ctx, e);
     ctx->step = step;
+    return LBM_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batches: many runs advanced by one persistent launch per step
+// ---------------------------------------------------------------------------
+
+struct lbm_batch {
+    int nruns = 0;
+    lbm_ctx** runs = nullptr;       // sub-contexts (own their buffers; share the stream)
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    cudaStream_t cap_stream = nullptr;
+    bool coupled = true;
+    lbm::FusedShape shape{128, 32};
+    int blocks = 0;                 // persistent grid size
+    int nitems = 0;                 // tiles over all runs
+    lbm::RunDesc* hdesc = nullptr;  // host copy of the run table
+    lbm::RunDesc* ddesc = nullptr;
+    int4* ditems = nullptr;
+    int* derr = nullptr;
+    int parity = 0;
+    bool desc_valid = false;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    int pending_error = LBM_OK;
+};
+
+namespace {
+
+void batch_drop_graphs(lbm_batch* b) {
+    for (int k = 0; k < 2; ++k)
+        if (b->graph[k]) {
+            cudaGraphExecDestroy(b->graph[k]);
+            b->graph[k] = nullptr;
+        }
+}
+
+int batch_fail(lbm_batch* b, cudaError_t e) {
+    if (e == cudaSuccess) return LBM_OK;
+    cudaGetLastError();
+    b->pending_error = LBM_ERR_CUDA;
+    return LBM_ERR_CUDA;
+}
+
+// Tensor maps, tile list and persistent grid for the current launch shape.
+int batch_build_tiles(lbm_batch* b) {
+    batch_drop_graphs(b);
+    const int bx = b->shape.bx, tx = bx - 4;
+    const int nl = b->coupled ? 3 : 2;
+    int64_t total = 0;
+    for (int r = 0; r < b->nruns; ++r) {
+        const lbm_ctx* c = b->runs[r];
+        total += (int64_t)((c->kp.nx + tx - 1) / tx) * ((c->kp.ny + b->shape.seg - 1) / b->shape.seg);
+    }
+    if (total > (int64_t)1 << 30) return LBM_ERR_INVALID_ARG;
+    int4* items = (int4*)std::malloc(sizeof(int4) * (size_t)total);
+    if (!items) return LBM_ERR_NOMEM;
+    // larger runs first: the tail of the persistent loop is made of small tiles
+    int* order = (int*)std::malloc(sizeof(int) * (size_t)b->nruns);
+    if (!order) {
+        std::free(items);
+        return LBM_ERR_NOMEM;
+    }
+    for (int r = 0; r < b->nruns; ++r) order[r] = r;
+    for (int a = 1; a < b->nruns; ++a) {  // insertion sort by cell count, stable
+        const int v = order[a];
+        const int64_t cv = (int64_t)b->runs[v]->kp.nx * b->runs[v]->kp.ny;
+        int k = a - 1;
+        while (k >= 0 && (int64_t)b->runs[order[k]]->kp.nx * b->runs[order[k]]->kp.ny < cv) {
+            order[k + 1] = order[k];
+            --k;
+        }
+        order[k + 1] = v;
+    }
+    int64_t n = 0;
+    for (int a = 0; a < b->nruns; ++a) {
+        const int r = order[a];
+        const lbm_ctx* c = b->runs[r];
+        const int nsx = (c->kp.nx + tx - 1) / tx, nsy = (c->kp.ny + b->shape.seg - 1) / b->shape.seg;
+        for (int sy = 0; sy < nsy; ++sy)
+            for (int sx = 0; sx < nsx; ++sx) items[n++] = make_int4(r, sx, sy, 0);
+    }
+    std::free(order);
+    for (int r = 0; r < b->nruns; ++r) {
+        lbm_ctx* c = b->runs[r];
+        lbm::RunDesc& d = b->hdesc[r];
+        for (int k = 0; k < 2; ++k) {
+            if (!lbm::make_tensor_map(&d.tmap[k], c->pop_alloc[k], c->kp, nl * 9, bx)) {
+                std::free(items);
+                return LBM_ERR_UNSUPPORTED;
+            }
+            d.pop[k] = c->ds.pop[k];
+        }
+        d.p = c->kp;
+        d.fields = c->ds.fields;
+        d.seg = b->shape.seg;
+        d.flip = c->cur ^ b->parity;
+    }
+    cudaFree(b->ditems);
+    b->ditems = nullptr;
+    cudaError_t e = cudaMalloc(&b->ditems, sizeof(int4) * (size_t)total);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(b->ditems, items, sizeof(int4) * (size_t)total, cudaMemcpyHostToDevice);
+    std::free(items);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(b->ddesc, b->hdesc, sizeof(lbm::RunDesc) * b->nruns, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return batch_fail(b, e);
+    b->nitems = (int)total;
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int per_sm = lbm::tma_batch_blocks_per_sm(bx, b->coupled);
+    b->blocks = (int)std::min<int64_t>(total, (int64_t)per_sm * (nsm > 0 ? nsm : 1));
+    b->desc_valid = true;
+    return LBM_OK;
+}
+
+// Re-upload the run table if a run was stepped, re-initialised or reloaded
+// on its own since the last batched step (its buffer parity or parameters
+// may differ from the table's).
+int batch_sync_desc(lbm_batch* b) {
+    bool dirty = !b->desc_valid;
+    for (int r = 0; r < b->nruns && !dirty; ++r) {
+        const lbm_ctx* c = b->runs[r];
+        dirty = b->hdesc[r].flip != (c->cur ^ b->parity) ||
+                std::memcmp(&b->hdesc[r].p, &c->kp, sizeof(lbm::KParams)) != 0;
+    }
+    if (!dirty) return LBM_OK;
+    for (int r = 0; r < b->nruns; ++r) {
+        b->hdesc[r].flip = b->runs[r]->cur ^ b->parity;
+        b->hdesc[r].p = b->runs[r]->kp;
+    }
+    cudaError_t e = cudaMemcpyAsync(b->ddesc, b->hdesc, sizeof(lbm::RunDesc) * b->nruns,
+                                    cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    b->desc_valid = true;
+    return batch_fail(b, e);
+}
+
+void batch_launch(lbm_batch* b, int parity, cudaStream_t st) {
+    lbm::launch_step_tma_batch(b->ddesc, b->ditems, b->nitems, b->blocks, b->shape.bx, b->coupled,
+                               parity, b->derr, st);
+}
+
+int batch_build_graph(lbm_batch* b, int parity) {
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return batch_fail(b, e);
+    int par = parity;
+    for (int s = 0; s < GRAPH_STEPS; ++s) {
+        batch_launch(b, par, b->cap_stream);
+        par ^= 1;
+    }
+    e = cudaStreamEndCapture(b->cap_stream, &g);
+    if (e != cudaSuccess) return batch_fail(b, e);
+    e = cudaGraphInstantiate(&b->graph[parity], g, 0);
+    cudaGraphDestroy(g);
+    return batch_fail(b, e);
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbm_batch_create(const lbm_params* params, int32_t nruns, void* stream, lbm_batch** out) {
+    if (!out) return LBM_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!params || nruns < 1) return LBM_ERR_INVALID_ARG;
+    for (int r = 0; r < nruns; ++r) {
+        const int v = validate(&params[r]);
+        if (v != LBM_OK) return v;
+        if (params[r].mode != params[0].mode) return LBM_ERR_INVALID_ARG;
+        if (params[r].kernel != LBM_KERNEL_AUTO && params[r].kernel != LBM_KERNEL_TMA)
+            return LBM_ERR_UNSUPPORTED;
+    }
+    if (!lbm::tma_available()) return LBM_ERR_UNSUPPORTED;
+    lbm_batch* b = new (std::nothrow) lbm_batch();
+    if (!b) return LBM_ERR_NOMEM;
+    b->coupled = params[0].mode == LBM_COUPLED;
+    if (stream) {
+        b->stream = (cudaStream_t)stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete b;
+            return LBM_ERR_CUDA;
+        }
+        b->own_stream = true;
+    }
+    b->runs = (lbm_ctx**)std::calloc((size_t)nruns, sizeof(lbm_ctx*));
+    b->hdesc = (lbm::RunDesc*)std::calloc((size_t)nruns, sizeof(lbm::RunDesc));
+    if (!b->runs || !b->hdesc) {
+        lbm_batch_destroy(b);
+        return LBM_ERR_NOMEM;
+    }
+    if (cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        lbm_batch_destroy(b);
+        return LBM_ERR_CUDA;
+    }
+    for (int r = 0; r < nruns; ++r) {
+        lbm_params pr = params[r];
+        pr.kernel = LBM_KERNEL_TMA;
+        const int rc = lbm_create(&pr, b->stream, &b->runs[r]);
+        if (rc != LBM_OK) {
+            lbm_batch_destroy(b);
+            return rc;
+        }
+        b->nruns = r + 1;
+    }
+    if (cudaMalloc(&b->ddesc, sizeof(lbm::RunDesc) * (size_t)nruns) != cudaSuccess ||
+        cudaMalloc(&b->derr, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        lbm_batch_destroy(b);
+        return LBM_ERR_NOMEM;
+    }
+    cudaMemset(b->derr, 0, sizeof(int));
+    const int rc = batch_build_tiles(b);
+    if (rc != LBM_OK) {
+        lbm_batch_destroy(b);
+        return rc;
+    }
+    *out = b;
+    return LBM_OK;
+}
+
+void lbm_batch_destroy(lbm_batch* b) {
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    batch_drop_graphs(b);
+    for (int r = 0; r < b->nruns; ++r) lbm_destroy(b->runs[r]);
+    std::free(b->runs);
+    std::free(b->hdesc);
+    cudaFree(b->ddesc);
+    cudaFree(b->ditems);
+    cudaFree(b->derr);
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+}
+
+int32_t lbm_batch_size(const lbm_batch* b) { return b ? b->nruns : LBM_ERR_INVALID_ARG; }
+
+lbm_ctx* lbm_batch_run(lbm_batch* b, int32_t run) {
+    if (!b || run < 0 || run >= b->nruns) return nullptr;
+    return b->runs[run];
+}
+
+int lbm_batch_step(lbm_batch* b, int64_t nsteps) {
+    if (!b || nsteps < 0) return LBM_ERR_INVALID_ARG;
+    int rc = batch_sync_desc(b);
+    if (rc != LBM_OK) return rc;
+    bool stall = false;
+    for (int r = 0; r < b->nruns; ++r) stall = stall || b->runs[r]->kp.stall_test;
+    int64_t left = nsteps;
+    while (left > 0) {
+        if (left >= GRAPH_STEPS && !stall) {
+            if (!b->graph[b->parity]) {
+                rc = batch_build_graph(b, b->parity);
+                if (rc != LBM_OK) return rc;
+            }
+            if (cudaGraphLaunch(b->graph[b->parity], b->stream) != cudaSuccess)
+                return batch_fail(b, cudaGetLastError());
+            left -= GRAPH_STEPS;  // even: parity unchanged
+        } else {
+            batch_launch(b, b->parity, b->stream);
+            b->parity ^= 1;
+            left -= 1;
+            if (stall) {  // the hook stalls one step only
+                for (int r = 0; r < b->nruns; ++r) b->hdesc[r].p.stall_test = 0;
+                cudaError_t e = cudaMemcpyAsync(b->ddesc, b->hdesc, sizeof(lbm::RunDesc) * b->nruns,
+                                                cudaMemcpyHostToDevice, b->stream);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+                if (e != cudaSuccess) return batch_fail(b, e);
+                stall = false;
+            }
+        }
+    }
+    // every run advanced by nsteps: its current buffer follows the batch parity
+    for (int r = 0; r < b->nruns; ++r) {
+        lbm_ctx* c = b->runs[r];
+        c->cur = b->parity ^ b->hdesc[r].flip;
+        c->step += nsteps;
+        if (c->kp.stall_test && nsteps > 0) {  // the one-shot test hook was taken by this call
+            c->kp.stall_test = 0;
+            drop_graphs(c);
+        }
+    }
+    return batch_fail(b, cudaGetLastError());
+}
+
+int lbm_batch_synchronize(lbm_batch* b) {
+    if (!b) return LBM_ERR_INVALID_ARG;
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return batch_fail(b, e);
+    int timed_out = 0;
+    e = cudaMemcpy(&timed_out, b->derr, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return batch_fail(b, e);
+    if (timed_out) {
+        cudaMemset(b->derr, 0, sizeof(int));
+        b->pending_error = LBM_OK;
+        return LBM_ERR_TIMEOUT;
+    }
+    const int pend = b->pending_error;
+    b->pending_error = LBM_OK;
+    return pend;
+}
+
+int lbm_batch_set_launch_shape(lbm_batch* b, int32_t tile_x, int32_t seg_y) {
+    if (!b) return LBM_ERR_INVALID_ARG;
+    if (tile_x != 0 && tile_x != 64 && tile_x != 128) return LBM_ERR_UNSUPPORTED;
+    if (seg_y != 0 && seg_y < 4) return LBM_ERR_INVALID_ARG;
+    const int rc = lbm_batch_synchronize(b);
+    if (rc != LBM_OK) return rc;
+    if (tile_x) b->shape.bx = tile_x;
+    if (seg_y) b->shape.seg = seg_y;
+    return batch_build_tiles(b);
+}
+
+int lbm_batch_get_launch_shape(const lbm_batch* b, int32_t* tile_x, int32_t* seg_y,
+                               int32_t* blocks, int32_t* tiles) {
+    if (!b) return LBM_ERR_INVALID_ARG;
+    if (tile_x) *tile_x = b->shape.bx;
+    if (seg_y) *seg_y = b->shape.seg;
+    if (blocks) *blocks = b->blocks;
+    if (tiles) *tiles = b->nitems;
+    return LBM_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Launch-shape autotuner: times candidate (block width, rows per block) pairs
+// on the live state, then puts the state back as it was.
+// ---------------------------------------------------------------------------
+
+namespace {
+
+int sm_count() {
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    return nsm > 0 ? nsm : 1;
+}
+
+// Rows per block worth trying for a grid of nx x ny: a fixed ladder plus the
+// values that fill one or two waves of resident blocks.
+int seg_candidates(int nx, int ny, int bx, int per_sm, int* out, int cap) {
+    int n = 0;
+    auto add = [&](int seg) {
+        if (seg < 4) seg = 4;
+        if (seg > ny && ny >= 4) seg = ny;
+        for (int k = 0; k < n; ++k)
+            if (out[k] == seg) return;
+        if (n < cap) out[n++] = seg;
+    };
+    const int ladder[] = {8, 16, 32, 64, 128};
+    for (int v : ladder) add(v);
+    const int strips = (nx + bx - 5) / (bx - 4);
+    const int slots = per_sm * sm_count();
+    for (int w = 1; w <= 2; ++w) {
+        const int nseg = (w * slots) / strips;
+        if (nseg >= 1) add((ny + nseg - 1) / nseg);
+    }
+    return n;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbm_autotune(lbm_ctx* ctx, int32_t steps, int32_t* tile_x, int32_t* seg_y,
+                 double* ms_per_step) {
+    if (!ctx || steps < 1) return LBM_ERR_INVALID_ARG;
+    if (ctx->kernel == LBM_KERNEL_SPLIT) return LBM_ERR_UNSUPPORTED;
+    int rc = lbm_synchronize(ctx);
+    if (rc != LBM_OK) return rc;
+    const size_t pop_bytes = sizeof(float) * (size_t)ctx->ds.nlat * 9 * (size_t)ctx->kp.plane;
+    float* snap = nullptr;
+    if (cudaMalloc(&snap, pop_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return LBM_ERR_NOMEM;
+    }
+    const int cur0 = ctx->cur;
+    const int64_t step0 = ctx->step;
+    const lbm::FusedShape shape0 = ctx->shape;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t ce = cudaMemcpy(snap, ctx->pop_alloc[cur0], pop_bytes, cudaMemcpyDeviceToDevice);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&e0);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+    double best = 1e300;
+    lbm::FusedShape best_shape = shape0;
+    const int bxs[2] = {128, 64};
+    const int nbx = ctx->kernel == LBM_KERNEL_TMA ? 2 : 1;
+    for (int a = 0; a < nbx && ce == cudaSuccess && rc == LBM_OK; ++a) {
+        const int bx = bxs[a];
+        const int per_sm =
+            ctx->kernel == LBM_KERNEL_TMA ? lbm::tma_blocks_per_sm(bx, ctx->kp.coupled) : 2;
+        int segs[8];
+        const int ns = seg_candidates(ctx->kp.nx, ctx->kp.ny, bx, per_sm, segs, 8);
+        for (int k = 0; k < ns && rc == LBM_OK; ++k) {
+            rc = lbm_set_launch_shape(ctx, bx, segs[k]);
+            if (rc != LBM_OK) break;
+            rc = lbm_step(ctx, 2);
+            if (rc == LBM_OK) rc = cuda_fail(ctx, cudaEventRecord(e0, ctx->stream));
+            if (rc == LBM_OK) rc = lbm_step(ctx, steps);
+            if (rc == LBM_OK) rc = cuda_fail(ctx, cudaEventRecord(e1, ctx->stream));
+            if (rc == LBM_OK) rc = lbm_synchronize(ctx);
+            float ms = 0.0f;
+            if (rc == LBM_OK) rc = cuda_fail(ctx, cudaEventElapsedTime(&ms, e0, e1));
+            if (rc == LBM_OK && ms / steps < best) {
+                best = ms / steps;
+                best_shape = lbm::FusedShape{bx, segs[k]};
+            }
+            // put the state back before the next candidate
+            ce = cudaMemcpy(ctx->pop_alloc[cur0], snap, pop_bytes, cudaMemcpyDeviceToDevice);
+            ctx->cur = cur0;
+            ctx->step = step0;
+            if (ce != cudaSuccess) break;
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(snap);
+    if (ce != cudaSuccess) return cuda_fail(ctx, ce);
+    const int rc2 = lbm_set_launch_shape(ctx, best_shape.bx, best_shape.seg);
+    if (rc != LBM_OK) return rc;
+    if (rc2 != LBM_OK) return rc2;
+    if (tile_x) *tile_x = best_shape.bx;
+    if (seg_y) *seg_y = best_shape.seg;
+    if (ms_per_step) *ms_per_step = best;
+    return LBM_OK;
+}
+
+int lbm_batch_autotune(lbm_batch* b, int32_t steps, int32_t* tile_x, int32_t* seg_y,
+                       double* ms_per_step) {
+    if (!b || steps < 1) return LBM_ERR_INVALID_ARG;
+    int rc = lbm_batch_synchronize(b);
+    if (rc != LBM_OK) return rc;
+    float** snap = (float**)std::calloc((size_t)b->nruns, sizeof(float*));
+    int* cur0 = (int*)std::calloc((size_t)b->nruns, sizeof(int));
+    int64_t* step0 = (int64_t*)std::calloc((size_t)b->nruns, sizeof(int64_t));
+    if (!snap || !cur0 || !step0) {
+        std::free(snap);
+        std::free(cur0);
+        std::free(step0);
+        return LBM_ERR_NOMEM;
+    }
+    cudaError_t ce = cudaSuccess;
+    auto bytes_of = [&](int r) {
+        const lbm_ctx* c = b->runs[r];
+        return sizeof(float) * (size_t)c->ds.nlat * 9 * (size_t)c->kp.plane;
+    };
+    for (int r = 0; r < b->nruns && ce == cudaSuccess; ++r) {
+        cur0[r] = b->runs[r]->cur;
+        step0[r] = b->runs[r]->step;
+        ce = cudaMalloc(&snap[r], bytes_of(r));
+        if (ce == cudaSuccess)
+            ce = cudaMemcpy(snap[r], b->runs[r]->pop_alloc[cur0[r]], bytes_of(r),
+                            cudaMemcpyDeviceToDevice);
+    }
+    const lbm::FusedShape shape0 = b->shape;
+    lbm::FusedShape best_shape = shape0;
+    double best = 1e300;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (ce == cudaSuccess) ce = cudaEventCreate(&e0);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+    const int bxs[2] = {128, 64};
+    const int segs[7] = {16, 24, 32, 48, 64, 96, 128};
+    for (int a = 0; a < 2 && ce == cudaSuccess && rc == LBM_OK; ++a) {
+        for (int k = 0; k < 7 && rc == LBM_OK; ++k) {
+            rc = lbm_batch_set_launch_shape(b, bxs[a], segs[k]);
+            if (rc != LBM_OK) break;
+            rc = lbm_batch_step(b, 2);
+            if (rc == LBM_OK) rc = batch_fail(b, cudaEventRecord(e0, b->stream));
+            if (rc == LBM_OK) rc = lbm_batch_step(b, steps);
+            if (rc == LBM_OK) rc = batch_fail(b, cudaEventRecord(e1, b->stream));
+            if (rc == LBM_OK) rc = lbm_batch_synchronize(b);
+            float ms = 0.0f;
+            if (rc == LBM_OK) rc = batch_fail(b, cudaEventElapsedTime(&ms, e0, e1));
+            if (rc == LBM_OK && ms / steps < best) {
+                best = ms / steps;
+                best_shape = lbm::FusedShape{bxs[a], segs[k]};
+            }
+            for (int r = 0; r < b->nruns && ce == cudaSuccess; ++r) {
+                ce = cudaMemcpy(b->runs[r]->pop_alloc[cur0[r]], snap[r], bytes_of(r),
+                                cudaMemcpyDeviceToDevice);
+                b->runs[r]->cur = cur0[r];
+                b->runs[r]->step = step0[r];
+            }
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    for (int r = 0; r < b->nruns; ++r) cudaFree(snap[r]);
+    std::free(snap);
+    std::free(cur0);
+    std::free(step0);
+    if (ce != cudaSuccess) return batch_fail(b, ce);
+    const int rc2 = lbm_batch_set_launch_shape(b, best_shape.bx, best_shape.seg);
+    if (rc != LBM_OK) return rc;
+    if (rc2 != LBM_OK) return rc2;
+    if (tile_x) *tile_x = best_shape.bx;
+    if (seg_y) *seg_y = best_shape.seg;
+    if (ms_per_step) *ms_per_step = best;
     return LBM_OK;
 }
 

@@ -95,6 +95,69 @@ struct CellOut {
     float ux, uy, dP;
 };
 
+// Flow part of one cell's collisions (App. D): forces, velocity, pressure
+// and, with do_collide, the flow populations gg collided in place.
+__device__ __forceinline__ CellOut collide_flow_cell(const KParams& p, const CellGeom& g, int j,
+                                                     float gg[9], bool do_collide) {
+    CellOut o;
+    // surface-tension force, Eq. (Fs)
+    const float g2 = g.gm * g.gm;
+    const float nds = g.nx * g.sgx + g.ny * g.sgy;
+    const float Fsx = p.N_sigma * g2 * (-g.sig * g.kappa * g.nx + (g.sgx - g.nx * nds));
+    const float Fsy = p.N_sigma * g2 * (-g.sig * g.kappa * g.ny + (g.sgy - g.ny * nds));
+    const float Ftx = Fsx + p.fext_x, Fty = Fsy + p.fext_y;
+    const float rho = p.rho_uniform ? p.rho_a : lerp_phase(p, g.phi, p.rho_a, p.rho_b);
+    const float jx = (gg[1] - gg[3]) + (gg[5] - gg[6]) - (gg[7] - gg[8]);
+    const float jy = (gg[2] - gg[4]) + (gg[5] + gg[6]) - (gg[7] + gg[8]);
+    // cs2 rho u = sum e g + cs2 F_t / 2  (App. D).  The division uses the
+    // same rounded rho cs2 as the equilibrium, so j -> u -> rho cs2 u does
+    // not drift by the rounding of 1/3 every step.
+    const float R = rho * CS2;
+    o.ux = (jx + 0.5f * CS2 * Ftx) / R;
+    o.uy = (jy + 0.5f * CS2 * Fty) / R;
+    // F_p = -grad psi with psi = P* - rho cs2
+    float Fpx = -g.pgx, Fpy = -g.pgy;
+    if (!p.rho_uniform) {
+        const float drho = (p.rho_a - p.rho_b) * p.inv_dphi;
+        Fpx += CS2 * drho * g.fgx;
+        Fpy += CS2 * drho * g.fgy;
+    }
+    const float G = Fpx * o.ux + Fpy * o.uy;
+    o.dP = g.dps + 0.5f * G;  // P = sum g + sigma_00 / 2
+    if (do_collide) {
+        FlowMacro m;
+        m.ux = o.ux;
+        m.uy = o.uy;
+        m.rho = rho;
+        m.dPs = g.dps;
+        m.dP = o.dP;
+        m.Ftx = Ftx;
+        m.Fty = Fty;
+        m.Fpx = Fpx;
+        m.Fpy = Fpy;
+        m.w_nu = p.nu_uniform ? p.w_nu : rate_from_coeff(lerp_phase(p, g.phi, p.nu_a, p.nu_b));
+        collide_flow(gg, m, p.w_zeta);
+        wall_correct_flow(gg, p, j, rho);
+    }
+    return o;
+}
+
+// Scalar part of one cell's collisions: f (Sec. 3, App. C) and h (Sec. 2.2)
+// given the velocity; f and h enter as their first moments (the zeroth
+// moments are phi and c) and leave in deviation form df, dh (q = 1..8).
+__device__ __forceinline__ void collide_scalars_cell(const KParams& p, int phi_fx, float phi,
+                                                     float c, float nx, float ny, float ux,
+                                                     float uy, float fjx, float fjy, float hjx,
+                                                     float hjy, float df[9], float dh[9]) {
+    // Eq. (theta) and the theta_c of Eq. (ISS)
+    float theta, theta_c;
+    interface_coeffs(p, phi_fx, c, theta, theta_c);
+    collide_scalar_dev(phi, fjx, fjy, p.M_phi * theta * nx, p.M_phi * theta * ny, p.w_kappa, ux,
+                       uy, df);
+    collide_scalar_dev(c, hjx, hjy, p.D_s * theta_c * nx, p.D_s * theta_c * ny, p.w_chi, ux, uy,
+                       dh);
+}
+
 // The three collisions of one cell at row j.  f and h enter as their first
 // moments (the zeroth moments are g.phi and g.c) and leave as deviation-form
 // outputs df, dh (q = 1..8); the flow populations gg are collided in place.
@@ -104,60 +167,16 @@ __device__ __forceinline__ CellOut collide_cell(const KParams& p, const CellGeom
                                                 float fjy, float hjx, float hjy, float gg[9],
                                                 float df[9], float dh[9], bool do_collide) {
     CellOut o;
-    // Eq. (theta) and the theta_c of Eq. (ISS)
-    float theta, theta_c;
-    interface_coeffs(p, g.phi_fx, g.c, theta, theta_c);
     if (COUPLED) {
-        // surface-tension force, Eq. (Fs)
-        const float g2 = g.gm * g.gm;
-        const float nds = g.nx * g.sgx + g.ny * g.sgy;
-        const float Fsx = p.N_sigma * g2 * (-g.sig * g.kappa * g.nx + (g.sgx - g.nx * nds));
-        const float Fsy = p.N_sigma * g2 * (-g.sig * g.kappa * g.ny + (g.sgy - g.ny * nds));
-        const float Ftx = Fsx + p.fext_x, Fty = Fsy + p.fext_y;
-        const float rho = p.rho_uniform ? p.rho_a : lerp_phase(p, g.phi, p.rho_a, p.rho_b);
-        const float jx = (gg[1] - gg[3]) + (gg[5] - gg[6]) - (gg[7] - gg[8]);
-        const float jy = (gg[2] - gg[4]) + (gg[5] + gg[6]) - (gg[7] + gg[8]);
-        // cs2 rho u = sum e g + cs2 F_t / 2  (App. D).  The division uses the
-        // same rounded rho cs2 as the equilibrium, so j -> u -> rho cs2 u does
-        // not drift by the rounding of 1/3 every step.
-        const float R = rho * CS2;
-        o.ux = (jx + 0.5f * CS2 * Ftx) / R;
-        o.uy = (jy + 0.5f * CS2 * Fty) / R;
-        // F_p = -grad psi with psi = P* - rho cs2
-        float Fpx = -g.pgx, Fpy = -g.pgy;
-        if (!p.rho_uniform) {
-            const float drho = (p.rho_a - p.rho_b) * p.inv_dphi;
-            Fpx += CS2 * drho * g.fgx;
-            Fpy += CS2 * drho * g.fgy;
-        }
-        const float G = Fpx * o.ux + Fpy * o.uy;
-        o.dP = g.dps + 0.5f * G;  // P = sum g + sigma_00 / 2
-        if (do_collide) {
-            FlowMacro m;
-            m.ux = o.ux;
-            m.uy = o.uy;
-            m.rho = rho;
-            m.dPs = g.dps;
-            m.dP = o.dP;
-            m.Ftx = Ftx;
-            m.Fty = Fty;
-            m.Fpx = Fpx;
-            m.Fpy = Fpy;
-            m.w_nu = p.nu_uniform ? p.w_nu : rate_from_coeff(lerp_phase(p, g.phi, p.nu_a, p.nu_b));
-            collide_flow(gg, m, p.w_zeta);
-            wall_correct_flow(gg, p, j, rho);
-        }
+        o = collide_flow_cell(p, g, j, gg, do_collide);
     } else {
         o.ux = ux_fixed;
         o.uy = uy_fixed;
         o.dP = 0.0f;
     }
-    if (do_collide) {
-        collide_scalar_dev(g.phi, fjx, fjy, p.M_phi * theta * g.nx, p.M_phi * theta * g.ny,
-                           p.w_kappa, o.ux, o.uy, df);
-        collide_scalar_dev(g.c, hjx, hjy, p.D_s * theta_c * g.nx, p.D_s * theta_c * g.ny,
-                           p.w_chi, o.ux, o.uy, dh);
-    }
+    if (do_collide)
+        collide_scalars_cell(p, g.phi_fx, g.phi, g.c, g.nx, g.ny, o.ux, o.uy, fjx, fjy, hjx, hjy,
+                             df, dh);
     return o;
 }
 

@@ -26,6 +26,16 @@ struct FusedShape {
     int seg;   // rows per block
 };
 
+// One run of a batch, as the batched step kernel sees it.
+struct alignas(128) RunDesc {
+    CUtensorMap tmap[2];    // bulk-tensor maps over the run's two population buffers
+    KParams p;
+    float* pop[2];
+    float* fields;
+    int seg;                // rows per tile
+    int flip;               // the run reads buffer (parity ^ flip) at batch parity `parity`
+};
+
 // Launchers (all asynchronous on `st`).
 void launch_step_split(const KParams& p, const DevState& s, int src, cudaStream_t st);
 void launch_step_fused(const KParams& p, const DevState& s, int src, const FusedShape& sh,
@@ -38,6 +48,12 @@ size_t tma_smem_bytes(int bx, bool coupled);
 cudaError_t configure_tma_smem();
 void launch_step_tma(const KParams& p, const DevState& s, int src, const FusedShape& sh,
                      const CUtensorMap* maps, int* err, cudaStream_t st);
+// Batched step: one persistent launch over `nitems` tiles (int4: run, strip,
+// segment, unused) of runs sharing block width bx and lattice count.
+void launch_step_tma_batch(const RunDesc* runs, const int4* items, int nitems, int blocks,
+                           int bx, bool coupled, int src, int* err, cudaStream_t st);
+int tma_batch_blocks_per_sm(int bx, bool coupled);
+int tma_blocks_per_sm(int bx, bool coupled);
 // Fill the field planes (phi, c, dP*, sigma, n, |grad phi|) of the current state.
 void launch_fields(const KParams& p, const DevState& s, int src, cudaStream_t st);
 // Macroscopic outputs (float64, dense [ny][nx]) of the current state; needs launch_fields first.

@@ -72,3 +72,28 @@ __device__ __forceinline__ void tma_load_3d(void* smem_dst, const CUtensorMap* m
 }
 
 }  // namespace lbm
+
+namespace lbm {
+
+// Named barrier 1 over `nthreads` threads (a multiple of 32).  Unlike
+// __syncthreads, warps may arrive from different code paths, as the two
+// warp groups of the TMA sweep do.
+__device__ __forceinline__ void named_bar_sync(int nthreads) {
+    asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
+}
+
+// Named barrier 1 with an OR reduction of `v` over the arriving threads.
+__device__ __forceinline__ bool named_bar_or(bool v, int nthreads) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.or.pred q, 1, %2, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)v), "r"(nthreads)
+        : "memory");
+    return r != 0;
+}
+
+}  // namespace lbm

@@ -88,6 +88,20 @@ SIGNATURES = {
     "lbm_field_stats_noalloc": (ctypes.c_int, [_DP, _DP, _DP, _DP, ctypes.c_int32, ctypes.c_int32,
                                                ctypes.c_int32, ctypes.c_double, ctypes.c_double,
                                                _DP, _VP]),
+    "lbm_autotune": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                                    ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double)]),
+    "lbm_batch_create": (ctypes.c_int, [ctypes.POINTER(lbm_params), ctypes.c_int32, _VP,
+                                        ctypes.POINTER(_VP)]),
+    "lbm_batch_destroy": (None, [_VP]),
+    "lbm_batch_size": (ctypes.c_int32, [_VP]),
+    "lbm_batch_run": (_VP, [_VP, ctypes.c_int32]),
+    "lbm_batch_step": (ctypes.c_int, [_VP, ctypes.c_int64]),
+    "lbm_batch_synchronize": (ctypes.c_int, [_VP]),
+    "lbm_batch_set_launch_shape": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32]),
+    "lbm_batch_get_launch_shape": (ctypes.c_int, [_VP] + [ctypes.POINTER(ctypes.c_int32)] * 4),
+    "lbm_batch_autotune": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                                          ctypes.POINTER(ctypes.c_int32),
+                                          ctypes.POINTER(ctypes.c_double)]),
     "lbm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
 }
 
@@ -249,6 +263,68 @@ def lbm_field_stats_noalloc(phi, c, ux, uy, nx, ny, walls_y, beta, c_max, result
                                           _addr(result), stream), "lbm_field_stats_noalloc")
 
 
+def lbm_autotune(ctx, steps=32):
+    """Returns (tile_x, seg_y, ms_per_step) of the fastest launch shape (now set)."""
+    tx, sy, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
+    _check(load().lbm_autotune(ctx, int(steps), ctypes.byref(tx), ctypes.byref(sy),
+                               ctypes.byref(ms)), "lbm_autotune")
+    return tx.value, sy.value, ms.value
+
+
+def lbm_batch_create(params, stream: Optional[int] = None) -> int:
+    arr = (lbm_params * len(params))(*params)
+    out = _VP()
+    _check(load().lbm_batch_create(arr, len(params), stream, ctypes.byref(out)), "lbm_batch_create")
+    return out.value
+
+
+def lbm_batch_destroy(b) -> None:
+    load().lbm_batch_destroy(b)
+
+
+def lbm_batch_size(b) -> int:
+    n = load().lbm_batch_size(b)
+    if n < 0:
+        raise LBMError(n, "lbm_batch_size")
+    return n
+
+
+def lbm_batch_run(b, run: int) -> int:
+    ctx = load().lbm_batch_run(b, int(run))
+    if not ctx:
+        raise LBMError(LBM_ERR_INVALID_ARG, "lbm_batch_run")
+    return ctx
+
+
+def lbm_batch_step(b, nsteps: int):
+    _check(load().lbm_batch_step(b, int(nsteps)), "lbm_batch_step")
+
+
+def lbm_batch_synchronize(b):
+    _check(load().lbm_batch_synchronize(b), "lbm_batch_synchronize")
+
+
+def lbm_batch_set_launch_shape(b, tile_x=0, seg_y=0):
+    _check(load().lbm_batch_set_launch_shape(b, int(tile_x), int(seg_y)),
+           "lbm_batch_set_launch_shape")
+
+
+def lbm_batch_get_launch_shape(b):
+    """Returns (tile_x, seg_y, blocks, tiles)."""
+    v = [ctypes.c_int32() for _ in range(4)]
+    _check(load().lbm_batch_get_launch_shape(b, *[ctypes.byref(x) for x in v]),
+           "lbm_batch_get_launch_shape")
+    return tuple(x.value for x in v)
+
+
+def lbm_batch_autotune(b, steps=16):
+    """Returns (tile_x, seg_y, ms_per_step) of the fastest batched launch shape (now set)."""
+    tx, sy, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
+    _check(load().lbm_batch_autotune(b, int(steps), ctypes.byref(tx), ctypes.byref(sy),
+                                     ctypes.byref(ms)), "lbm_batch_autotune")
+    return tx.value, sy.value, ms.value
+
+
 def lbm_strerror(code: int) -> str:
     return load().lbm_strerror(code).decode()
 
@@ -270,16 +346,22 @@ def params_from(phys, dtype=LBM_F32, kernel=LBM_KERNEL_AUTO) -> lbm_params:
 class Sim:
     """A context plus numpy-facing helpers (all work runs in liblbm.so)."""
 
-    def __init__(self, phys, dtype=LBM_F32, kernel=LBM_KERNEL_AUTO, stream=None):
+    def __init__(self, phys, dtype=LBM_F32, kernel=LBM_KERNEL_AUTO, stream=None, ctx=None):
         self.nx, self.ny = int(phys.nx), int(phys.ny)
         self.mode = int(getattr(phys, "mode", 0))
         self.params = params_from(phys, dtype, kernel)
-        self.ctx = lbm_create(self.params, stream)
+        # a context handed in (a run of a batch) belongs to its owner
+        self._owned = ctx is None
+        self.ctx = lbm_create(self.params, stream) if ctx is None else ctx
 
     def close(self):
         if getattr(self, "ctx", None):
-            lbm_destroy(self.ctx)
+            if self._owned:
+                lbm_destroy(self.ctx)
             self.ctx = None
+
+    def autotune(self, steps=32):
+        return lbm_autotune(self.ctx, steps)
 
     def __del__(self):
         try:
@@ -332,3 +414,45 @@ class Sim:
 
     def load(self, path):
         lbm_load_state(self.ctx, path)
+
+
+class Batch:
+    """Runs advanced together by the batched kernel; ``runs[k]`` is a Sim view
+    of run k (owned by the batch) for initialisation, fields and diagnostics."""
+
+    def __init__(self, physics, dtype=LBM_F32, stream=None):
+        self.params = [params_from(ph, dtype, LBM_KERNEL_TMA) for ph in physics]
+        self.handle = lbm_batch_create(self.params, stream)
+        self.runs = [Sim(ph, dtype, LBM_KERNEL_TMA, ctx=lbm_batch_run(self.handle, k))
+                     for k, ph in enumerate(physics)]
+
+    def close(self):
+        if getattr(self, "handle", None):
+            for r in self.runs:
+                r.close()
+            lbm_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __len__(self):
+        return len(self.runs)
+
+    def step(self, n=1):
+        lbm_batch_step(self.handle, n)
+
+    def sync(self):
+        lbm_batch_synchronize(self.handle)
+
+    def set_launch_shape(self, tile_x=0, seg_y=0):
+        lbm_batch_set_launch_shape(self.handle, tile_x, seg_y)
+
+    def launch_shape(self):
+        return lbm_batch_get_launch_shape(self.handle)
+
+    def autotune(self, steps=16):
+        return lbm_batch_autotune(self.handle, steps)

@@ -210,6 +210,15 @@ def ensemble_draws(nruns=64, seed=CASE_SEED, grids=ENSEMBLE_GRIDS):
     return out
 
 
+def ensemble_case(draw, shrink=1, W=4.0, steps=20000) -> Case:
+    """Drop-in-shear case of one ensemble draw; `shrink` divides the grid (and
+    so R = H/5) for test-sized versions of the same ensemble."""
+    nx, ny = draw["nx"] // shrink, draw["ny"] // shrink
+    return shear_drop(nx, ny, ny / 5.0, W, Ca=draw["Ca"], beta=draw["beta"],
+                      Gamma0=draw["Gamma0"], Pe_s=draw["Pe_s"], steps=steps,
+                      name=f"ensemble_{nx}x{ny}")
+
+
 def lively_shear_drop(nx=100, ny=60, R=14.0, W=4.0, steps=400) -> Case:
     """A small, fast-evolving drop in shear used for parity tests: strong
     shear, tension and Marangoni stress so that every term moves within a few

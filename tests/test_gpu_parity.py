@@ -16,16 +16,9 @@ from paper_2504_09024_gb300 import lbm, workloads as W
 
 pytestmark = pytest.mark.gpu
 
-TOL = 1e-5
+from parity import TOL, check_lively, rel, umag
+
 KERNELS = [lbm.LBM_KERNEL_TMA, lbm.LBM_KERNEL_FUSED, lbm.LBM_KERNEL_SPLIT]
-
-
-def rel(a, b):
-    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
-
-
-def umag(F):
-    return np.hypot(F["ux"], F["uy"])
 
 
 def run_gpu(case, kernel, steps=None):
@@ -65,8 +58,8 @@ def test_static_drop_cos_mode_1000_steps(kernel):
 def test_lively_shear_drop_1000_steps(kernel):
     case = W.lively_shear_drop()
     got = run_gpu(case, kernel, 1000).fields()
-    errs = check_fields(got, oracle_fields(case, 1000))
     ref = oracle_fields(case, 1000)
+    errs = check_lively(got, ref)
     assert rel(got["P"], ref["P"]) < 1e-6, errs
 
 
@@ -229,7 +222,7 @@ def test_checkpoint_resume_bit_exact():
         path = os.path.join(d, "ck.bin")
         s.save(path)
         s.close()
-        t = lbm.Sim(case.phys)
+        t = lbm.Sim(case.phys, kernel=lbm.LBM_KERNEL_FUSED)
         t.load(path)
         assert t.t == 100
         t.step(100)
