@@ -39,6 +39,10 @@ struct TmaLayout {
 
 __device__ __forceinline__ int rmod(int a, int m) { return ((a % m) + m) % m; }
 
+// x mod m for 0 <= x < 2m
+template <int M>
+__device__ __forceinline__ int wrap_once(int x) { return x >= M ? x - M : x; }
+
 }  // namespace
 
 // Shared-memory carve-up of one block (the barriers come first).
@@ -151,8 +155,9 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap* tmap, const KParam
     constexpr int NT = 2 * BX;  // threads meeting at the phase barriers
 
     // The row loop of one warp group (each group runs its own copy, so each
-    // holds only its own registers; the phase barriers are named barriers
-    // that both copies reach the same number of times).
+    // holds only its own registers).  Named barrier 1 (both groups, once per
+    // row) publishes the moments of row r; named barrier 2 (flow group only)
+    // publishes its normals to its own collisions.
     auto rows = [&](auto group) -> bool {
         constexpr bool FLOW = decltype(group)::value;
         // values kept for the collisions, newest row first: group 0 keeps
@@ -160,10 +165,14 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap* tmap, const KParam
         // flow populations of rows r .. r-2
         float ks[4][5];
         float kg[3][9];
-        for (int r = rs; r <= re + 1; ++r) {
+        // ring slots of row r, advanced with the loop (rows r-k sit at
+        // wrap_once(s5 + T_RING - k) and wrap_once(s3 + T_NRING - k))
+        int s5 = rmod(rs, T_RING), s3 = rmod(rs, T_NRING);
+        for (int r = rs; r <= re + 1;
+             ++r, s5 = wrap_once<T_RING>(s5 + 1), s3 = wrap_once<T_NRING>(s3 + 1)) {
             const bool sweep = r <= re;  // the last pass only finishes the scalar collisions
             const bool phys = sweep && (!p.walls || r < p.ny);
-            const int slot = rmod(r, T_RING);
+            const int slot = s5;
             // ---------------- A: moments of row r ----------------
             if (phys) {
                 bool ok = true;
@@ -243,7 +252,7 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap* tmap, const KParam
                         s_dps[slot * BX + t] = s_dps[ss * BX + t];
                     }
                 }
-                named_bar_sync(NT);
+                named_bar_or(false, NT);
             }
             // ---------------- B: unit normal one row behind ----------------
             if (FLOW && sweep) {
@@ -257,8 +266,10 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap* tmap, const KParam
                         continue;
                     }
                     if (role >= 2 && rn >= y0 - 1 && rn <= y1) {
-                        const int sm1 = rmod(rn - 1, T_RING), s0 = rmod(rn, T_RING),
-                                  sp1 = rmod(rn + 1, T_RING);
+                        // pass 0: rows r-2, r-1, r
+                        const int sm1 = pass ? rmod(rn - 1, T_RING) : wrap_once<T_RING>(s5 + 3);
+                        const int s0 = pass ? rmod(rn, T_RING) : wrap_once<T_RING>(s5 + 4);
+                        const int sp1 = pass ? rmod(rn + 1, T_RING) : s5;
                         int v[3][3];
 #pragma unroll
                         for (int e = 0; e < 3; ++e) {
@@ -269,23 +280,25 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap* tmap, const KParam
                         float gx, gy, nx, ny, gm;
                         iso_grad_fx(v, p.fx_inv[0], gx, gy);
                         unit_normal(gx, gy, nx, ny, gm);
-                        const int ns = rmod(rn, T_NRING);
+                        const int ns = pass ? rmod(rn, T_NRING) : wrap_once<T_NRING>(s3 + 2);
                         s_nx[ns * BX + t] = nx;
                         s_ny[ns * BX + t] = ny;
                         s_gm[ns * BX + t] = gm;
                     }
                 }
             }
-            named_bar_sync(NT);
+            // the flow group's own barrier: its collisions read the normals
+            // its other warps just formed (group 0 does not wait here)
+            if constexpr (FLOW) named_bar_sync<2>(BX);
             // ---------------- C: collisions ----------------
             if constexpr (FLOW) {
                 // flow lattice of row r-2; its velocity goes to the ring for group 0
                 const int jc = r - 2;
                 if (COUPLED && role == 3 && jc >= y0 && jc < y1) {
-                    const int c0 = rmod(jc, T_RING);
-                    const int cr[3] = {rmod(jc - 1, T_RING), c0, rmod(jc + 1, T_RING)};
-                    const int nr[3] = {rmod(jc - 1, T_NRING), rmod(jc, T_NRING),
-                                       rmod(jc + 1, T_NRING)};
+                    // rows jc - 1, jc, jc + 1 = r - 3, r - 2, r - 1
+                    const int c0 = wrap_once<T_RING>(s5 + 3);
+                    const int cr[3] = {wrap_once<T_RING>(s5 + 2), c0, wrap_once<T_RING>(s5 + 4)};
+                    const int nr[3] = {s3, wrap_once<T_NRING>(s3 + 1), wrap_once<T_NRING>(s3 + 2)};
                     CellGeom g;
                     g.phi_fx = s_phi[c0 * BX + t];
                     g.phi = (float)g.phi_fx * p.fx_inv[0];
@@ -342,7 +355,7 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap* tmap, const KParam
                 // scalar lattices of row r-3, one row behind the flow
                 const int jc = r - 3;
                 if (role == 3 && jc >= y0 && jc < y1) {
-                    const int c0 = rmod(jc, T_RING), n0 = rmod(jc, T_NRING);
+                    const int c0 = wrap_once<T_RING>(s5 + 2), n0 = s3;  // row r - 3
                     const int phi_fx = s_phi[c0 * BX + t];
                     const int64_t idx = (int64_t)jc * p.pitch + i;
                     float ux, uy;

@@ -75,11 +75,13 @@ __device__ __forceinline__ void tma_load_3d(void* smem_dst, const CUtensorMap* m
 
 namespace lbm {
 
-// Named barrier 1 over `nthreads` threads (a multiple of 32).  Unlike
-// __syncthreads, warps may arrive from different code paths, as the two
-// warp groups of the TMA sweep do.
+// Named barrier `id` (1..15) over `nthreads` threads (a multiple of 32).
+// Unlike __syncthreads, warps may arrive from different code paths, as the
+// two warp groups of the TMA sweep do.  A barrier id is used with one kind
+// of barrier instruction only (bar.sync here, bar.red in named_bar_or).
+template <int ID>
 __device__ __forceinline__ void named_bar_sync(int nthreads) {
-    asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
+    asm volatile("bar.sync %0, %1;" ::"n"(ID), "r"(nthreads) : "memory");
 }
 
 // Named barrier 1 with an OR reduction of `v` over the arriving threads.
