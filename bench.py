@@ -31,7 +31,10 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-BYTES_PER_CELL = {"f32": 216, "f16s": 124, "bf16s": 124}  # algorithmic bytes per coupled cell update
+# algorithmic bytes per coupled cell update: 27 populations read and written
+# once (the 16-bit format also moves two 32-bit zeroth moments per cell,
+# 120 B in all, which count as traffic above the algorithmic figure)
+BYTES_PER_CELL = {"f32": 216, "f16s": 108, "bf16s": 108}
 METRIC = "coupled MLUPS"
 UNIT = "MLUPS"
 
@@ -206,6 +209,124 @@ def run_reference(args, rank, world):
     return 0
 
 
+def run_ensemble(args, rank, world, local_rank):
+    """Batched ensemble of drop-in-shear runs (uneven grids, one persistent
+    launch per step for all runs).  value = cell updates of all runs per
+    second; runs_per_hour converts the step time to runs of RUN_STEPS steps."""
+    import torch
+    from paper_2504_09024_gb300 import lbm, workloads as W
+
+    RUN_STEPS = 20000
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist  # noqa: F811
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    nruns = int(args.workload[len("ensemble"):] or 64)
+    # every rank runs its own draw of the ensemble (weak scaling over replicas)
+    draws = W.ensemble_draws(nruns=nruns, seed=W.CASE_SEED + rank)
+    cases = [W.ensemble_case(d, steps=RUN_STEPS) for d in draws]
+    ncell = sum(c.phys.nx * c.phys.ny for c in cases)
+    stream = torch.cuda.Stream()
+    b = lbm.Batch([c.phys for c in cases], stream=stream.cuda_stream)
+    for r, c in zip(b.runs, cases):
+        r.init(c.phi, c.c, c.ux, c.uy)
+    if args.tile_x or args.seg_y:
+        b.set_launch_shape(args.tile_x, args.seg_y)
+        tuned = None
+    else:
+        tx, sy, tms = b.autotune(steps=8)
+        tuned = {"tile_x": tx, "seg_y": sy, "ms_per_step": tms}
+    bx, seg, blocks, tiles = b.launch_shape()
+    b.step(args.warmup)
+    b.sync()
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    time.sleep(0.3)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    b.step(args.steps)
+    e1.record(stream)
+    e1.synchronize()
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    clk = clocks.stop()
+    t = torch.tensor([e0.elapsed_time(e1)], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    ms_step = ms_max / args.steps
+    value = world * ncell * args.steps / (ms_max * 1e-3) / 1e6
+
+    # end to end through the public API: every run initialised from pinned
+    # host fields, K batched steps, every run's fields read back + diagnostics
+    host_in = [[torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+                for a in (c.phi, c.c, c.ux, c.uy)] for c in cases]
+    host_out = [[torch.empty((c.phys.ny, c.phys.nx), dtype=torch.float64).pin_memory()
+                 for _ in range(5)] for c in cases]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for r, hin in zip(b.runs, host_in):
+        lbm.lbm_init_fields(r.ctx, *hin)
+    b.step(args.steps)
+    diags = []
+    for r, hout in zip(b.runs, host_out):
+        lbm.lbm_get_fields(r.ctx, *hout)
+        diags.append(r.diagnostics())
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    e2e_s = float(t.item())
+    h2d = sum(a.numel() * 8 for h in host_in for a in h)
+    d2h = sum(a.numel() * 8 for h in host_out for a in h) + 128 * len(cases)
+
+    peak, peak_kind = peaks()
+    bpc = BYTES_PER_CELL[args.dtype]
+    achieved = bpc * ncell / (ms_step * 1e-3) / 1e9
+    grids = {}
+    for c in cases:
+        k = f"{c.phys.nx}x{c.phys.ny}"
+        grids[k] = grids.get(k, 0) + 1
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
+        "config": {"workload": f"ensemble of {nruns} drop-in-shear runs", "runs": nruns,
+                   "grids": grids, "cells_per_step": ncell, "kernel": "k_sweep_tma_batch",
+                   "launch_shape": [bx, seg], "persistent_blocks": blocks, "tiles": tiles,
+                   "launch_shape_from": "lbm_batch_autotune" if tuned else "command line",
+                   "l2": "populations exceed the 129 MB L2; no flush",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "runs_per_hour": world * nruns * 3600.0 / (RUN_STEPS * ms_step * 1e-3),
+        "run_steps": RUN_STEPS,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_kind": f"{peak_kind} hbm_gbs",
+                     "bytes_per_cell": bpc, "traffic": None},
+        "e2e": {"value": world * ncell * args.steps / e2e_s / 1e6, "unit": UNIT,
+                "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+                "what": "lbm_init_fields of every run from pinned host fields + "
+                        "lbm_batch_step(K) + lbm_get_fields and lbm_diagnostics of every run"},
+        "gpu_launches": args.steps,
+        "clocks": clk,
+        "check": {"nonfinite": int(sum(d["nonfinite"] for d in diags))},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(cases[0], args.cpu_budget)
+    b.close()
+    if rank == 0:
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     from paper_2504_09024_gb300 import lbm
@@ -290,6 +411,8 @@ def run_ours(args, rank, world, local_rank):
     achieved = bpc * ncell / (ms_step * 1e-3) / 1e9
     kname = {lbm.LBM_KERNEL_TMA: "k_sweep_tma", lbm.LBM_KERNEL_FUSED: "k_fused_sweep",
              lbm.LBM_KERNEL_SPLIT: "k_collide"}[lbm.lbm_kernel_in_use(sim.ctx)]
+    if args.dtype != "f32":
+        kname = "k_sweep_tma16"
     tr = traffic_record(kname)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -345,6 +468,8 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", 0))
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.workload.startswith("ensemble"):
+        return run_ensemble(args, rank, world, local_rank)
     return run_ours(args, rank, world, local_rank)
 
 

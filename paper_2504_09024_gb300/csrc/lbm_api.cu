@@ -43,6 +43,11 @@ struct lbm_ctx {
     int diag_nb = 0;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     CUtensorMap tmaps[2];   // bulk-tensor maps over the two population buffers
+    // 16-bit storage: the state lives in pop16 (word planes, lbm_store16.cuh);
+    // the FP32 buffers stage initialisation and field output
+    int st = lbm::ST_F32;
+    float* pop16_alloc[2] = {nullptr, nullptr};
+    unsigned* dstep = nullptr;  // step counter of the stochastic rounding (16-bit)
     int* derr = nullptr;    // device flag: a bounded wait expired
     int pending_error = LBM_OK;
 };
@@ -91,10 +96,11 @@ int validate(const lbm_params* p) {
     if (p->mode != LBM_COUPLED && p->mode != LBM_FIXED_U) return LBM_ERR_INVALID_ARG;
     if (p->kernel < LBM_KERNEL_AUTO || p->kernel > LBM_KERNEL_TMA) return LBM_ERR_INVALID_ARG;
     if (p->reserved != 0) return LBM_ERR_INVALID_ARG;
-    if (p->dtype != LBM_F32) {
-        if (p->dtype == LBM_F16S || p->dtype == LBM_BF16S) return LBM_ERR_UNSUPPORTED;
+    if (p->dtype != LBM_F32 && p->dtype != LBM_F16S && p->dtype != LBM_BF16S)
         return LBM_ERR_INVALID_ARG;
-    }
+    // 16-bit storage runs on the TMA sweep only
+    if (p->dtype != LBM_F32 && p->kernel != LBM_KERNEL_AUTO && p->kernel != LBM_KERNEL_TMA)
+        return LBM_ERR_UNSUPPORTED;
     if (!(p->W > 0.0) || p->phi_a == p->phi_b || !(p->c_max > 0.0)) return LBM_ERR_INVALID_ARG;
     if (!(p->M_phi > 0.0) || !(p->D_s > 0.0)) return LBM_ERR_RATE;
     if (p->mode == LBM_COUPLED) {
@@ -154,10 +160,37 @@ lbm::KParams make_kparams(const lbm_params& p) {
     k.phi_a_fx = (int)std::llround(p.phi_a * k.fx_scale[0]);
     k.phi_b_fx = (int)std::llround(p.phi_b * k.fx_scale[0]);
     k.phi_m_fx = (int)std::llround(0.5 * (p.phi_a + p.phi_b) * k.fx_scale[0]);
+    // 16-bit deviations: per-lattice power-of-two scales that bring the
+    // expected largest deviation (a third of the largest first moment:
+    // |u| + flux of the interface terms) near 1; FP16 only (BF16 has the FP32
+    // exponent range).  k <= 14 keeps |d| up to 4 below FP16's 65504.
+    const double U = std::fabs(p.u_wall);
+    const double dphi_abs = std::fabs(p.phi_a - p.phi_b);
+    const double mag[3] = {(U + p.M_phi / p.W) * dphi_abs / 3.0,
+                           p.c_max * (U + 4.0 * p.D_s / p.W) / 3.0,
+                           (U + 1e-6) / 3.0};
+    for (int l = 0; l < 3; ++l) {
+        int e = 0;
+        if (p.dtype == LBM_F16S) {
+            const double m = std::fmax(mag[l], std::ldexp(1.0, -14));
+            e = (int)std::floor(std::log2(1.0 / m));
+            e = e < 0 ? 0 : (e > 14 ? 14 : e);
+        }
+        k.qs[l] = (float)std::ldexp(1.0, e);
+        k.qinv[l] = (float)std::ldexp(1.0, -e);
+    }
     return k;
 }
 
-void launch_one_step(lbm_ctx* ctx, int src, cudaStream_t st) {
+void launch_one_step(lbm_ctx* ctx, int src, cudaStream_t st, int step_off = 0) {
+    if (ctx->st != lbm::ST_F32) {
+        lbm::KParams kp = ctx->kp;
+        kp.step_off = step_off;
+        lbm::launch_step_tma16(kp, ctx->pop16_alloc[src] + lbm::XGHOST,
+                               ctx->pop16_alloc[1 - src] + lbm::XGHOST, ctx->ds.fields, ctx->shape,
+                               ctx->tmaps[src], ctx->st, ctx->derr, st);
+        return;
+    }
     if (ctx->kernel == LBM_KERNEL_SPLIT)
         lbm::launch_step_split(ctx->kp, ctx->ds, src, st);
     else if (ctx->kernel == LBM_KERNEL_TMA)
@@ -168,12 +201,41 @@ void launch_one_step(lbm_ctx* ctx, int src, cudaStream_t st) {
 
 int build_tensor_maps(lbm_ctx* ctx) {
     if (ctx->kernel != LBM_KERNEL_TMA) return LBM_OK;
-    const int nplanes = ctx->ds.nlat * 9;
-    for (int b = 0; b < 2; ++b)
-        if (!lbm::make_tensor_map(&ctx->tmaps[b], ctx->pop_alloc[b], ctx->kp, nplanes,
-                                  ctx->shape.bx))
+    const int nplanes = lbm::store_planes(ctx->st, ctx->kp.coupled);
+    for (int b = 0; b < 2; ++b) {
+        float* base = ctx->st == lbm::ST_F32 ? ctx->pop_alloc[b] : ctx->pop16_alloc[b];
+        if (!lbm::make_tensor_map(&ctx->tmaps[b], base, ctx->kp, nplanes, ctx->shape.bx))
             return LBM_ERR_UNSUPPORTED;
+    }
     return LBM_OK;
+}
+
+// The device step counter of the stochastic rounding follows ctx->step
+// (asynchronous on the context stream; no-op for FP32 storage).
+void sync_step_ctr(lbm_ctx* ctx) {
+    if (!ctx->dstep) return;
+    static_assert(sizeof(unsigned) == 4, "32-bit counter");
+    const unsigned v = (unsigned)ctx->step;
+    cudaMemcpyAsync(ctx->dstep, &v, sizeof(unsigned), cudaMemcpyHostToDevice, ctx->stream);
+    cudaStreamSynchronize(ctx->stream);
+}
+
+// Words of one state buffer (the current storage format).
+size_t state_words(const lbm_ctx* ctx) {
+    return (size_t)lbm::store_planes(ctx->st, ctx->kp.coupled) * (size_t)ctx->kp.plane;
+}
+
+float* state_alloc(lbm_ctx* ctx, int b) {
+    return ctx->st == lbm::ST_F32 ? ctx->pop_alloc[b] : ctx->pop16_alloc[b];
+}
+
+// The current state in FP32 deviation form, in buffer `b` of the FP32 pair
+// (16-bit storage: expanded into FP32 buffer 0).  Returns the FP32 buffer index.
+int fp32_view(lbm_ctx* ctx) {
+    if (ctx->st == lbm::ST_F32) return ctx->cur;
+    lbm::launch_unpack16(ctx->kp, ctx->pop16_alloc[ctx->cur], ctx->pop_alloc[0], ctx->st,
+                         ctx->stream);
+    return 0;
 }
 
 int build_graph(lbm_ctx* ctx, int parity) {
@@ -182,9 +244,10 @@ int build_graph(lbm_ctx* ctx, int parity) {
     if (e != cudaSuccess) return cuda_fail(ctx, e);
     int src = parity;
     for (int s = 0; s < GRAPH_STEPS; ++s) {
-        launch_one_step(ctx, src, ctx->cap_stream);
+        launch_one_step(ctx, src, ctx->cap_stream, s);
         src ^= 1;
     }
+    if (ctx->dstep) lbm::launch_step_advance(ctx->dstep, GRAPH_STEPS, ctx->cap_stream);
     e = cudaStreamEndCapture(ctx->cap_stream, &g);
     if (e != cudaSuccess) return cuda_fail(ctx, e);
     e = cudaGraphInstantiate(&ctx->graph[parity], g, 0);
@@ -250,6 +313,7 @@ int lbm_create(const lbm_params* p, void* stream, lbm_ctx** out) {
     ctx->kernel = p->kernel == LBM_KERNEL_AUTO ? (lbm::tma_available() ? LBM_KERNEL_TMA
                                                                        : LBM_KERNEL_FUSED)
                                                : p->kernel;
+    ctx->st = p->dtype == LBM_F16S ? lbm::ST_F16 : (p->dtype == LBM_BF16S ? lbm::ST_BF16 : lbm::ST_F32);
     if (ctx->kernel == LBM_KERNEL_TMA && !lbm::tma_available()) {
         delete ctx;
         return LBM_ERR_UNSUPPORTED;
@@ -268,7 +332,8 @@ int lbm_create(const lbm_params* p, void* stream, lbm_ctx** out) {
         lbm_destroy(ctx);
         return LBM_ERR_CUDA;
     }
-    if (lbm::configure_fused_smem() != cudaSuccess || lbm::configure_tma_smem() != cudaSuccess) {
+    if (lbm::configure_fused_smem() != cudaSuccess || lbm::configure_tma_smem() != cudaSuccess ||
+        lbm::configure_tma16_smem() != cudaSuccess) {
         cudaGetLastError();
         lbm_destroy(ctx);
         return LBM_ERR_CUDA;
@@ -282,11 +347,19 @@ int lbm_create(const lbm_params* p, void* stream, lbm_ctx** out) {
         cudaMalloc(&ctx->fields_alloc, fld_bytes) != cudaSuccess ||
         cudaMalloc(&ctx->dpartial, sizeof(double) * lbm::DIAG_NSUM * ctx->diag_nb) != cudaSuccess ||
         cudaMalloc(&ctx->dresult, sizeof(double) * 16) != cudaSuccess ||
-        cudaMalloc(&ctx->derr, sizeof(int)) != cudaSuccess) {
+        cudaMalloc(&ctx->derr, sizeof(int)) != cudaSuccess ||
+        (ctx->st != lbm::ST_F32 &&
+         (cudaMalloc(&ctx->dstep, sizeof(unsigned)) != cudaSuccess ||
+          cudaMalloc(&ctx->pop16_alloc[0], sizeof(float) * state_words(ctx)) != cudaSuccess ||
+          cudaMalloc(&ctx->pop16_alloc[1], sizeof(float) * state_words(ctx)) != cudaSuccess))) {
         cudaGetLastError();
         lbm_destroy(ctx);
         return LBM_ERR_NOMEM;
     }
+    for (int b = 0; b < 2 && ctx->st != lbm::ST_F32; ++b)
+        cudaMemsetAsync(ctx->pop16_alloc[b], 0, sizeof(float) * state_words(ctx), ctx->stream);
+    ctx->kp.step_ctr = ctx->dstep;
+    if (ctx->dstep) cudaMemsetAsync(ctx->dstep, 0, sizeof(unsigned), ctx->stream);
     // a defined state before initialisation
     for (int b = 0; b < 2; ++b) ctx->ds.pop[b] = ctx->pop_alloc[b] + lbm::XGHOST;
     ctx->ds.fields = ctx->fields_alloc + lbm::XGHOST;
@@ -317,6 +390,9 @@ void lbm_destroy(lbm_ctx* ctx) {
     cudaFree(ctx->dpartial);
     cudaFree(ctx->dresult);
     cudaFree(ctx->derr);
+    cudaFree(ctx->pop16_alloc[0]);
+    cudaFree(ctx->pop16_alloc[1]);
+    cudaFree(ctx->dstep);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
@@ -326,8 +402,11 @@ int lbm_init_fields_device(lbm_ctx* ctx, const double* phi, const double* c, con
                            const double* uy, const double* P) {
     if (!ctx || !phi || !c || !ux || !uy) return LBM_ERR_INVALID_ARG;
     lbm::launch_init(ctx->kp, ctx->ds, 0, phi, c, ux, uy, P, ctx->stream);
+    if (ctx->st != lbm::ST_F32)
+        lbm::launch_pack16(ctx->kp, ctx->pop_alloc[0], ctx->pop16_alloc[0], ctx->st, ctx->stream);
     ctx->cur = 0;
     ctx->step = 0;
+    sync_step_ctr(ctx);
     return check_launch(ctx);
 }
 
@@ -369,6 +448,7 @@ int lbm_step(lbm_ctx* ctx, int64_t nsteps) {
             nsteps -= GRAPH_STEPS;
         } else {
             launch_one_step(ctx, ctx->cur, ctx->stream);
+            if (ctx->dstep) lbm::launch_step_advance(ctx->dstep, 1, ctx->stream);
             ctx->cur ^= 1;
             ctx->step += 1;
             nsteps -= 1;
@@ -384,8 +464,9 @@ int lbm_step(lbm_ctx* ctx, int64_t nsteps) {
 int lbm_get_fields_device(lbm_ctx* ctx, double* phi, double* c, double* ux, double* uy,
                           double* P) {
     if (!ctx) return LBM_ERR_INVALID_ARG;
-    lbm::launch_fields(ctx->kp, ctx->ds, ctx->cur, ctx->stream);
-    lbm::launch_macro_out(ctx->kp, ctx->ds, ctx->cur, phi, c, ux, uy, P, ctx->stream);
+    const int b = fp32_view(ctx);
+    lbm::launch_fields(ctx->kp, ctx->ds, b, ctx->stream);
+    lbm::launch_macro_out(ctx->kp, ctx->ds, b, phi, c, ux, uy, P, ctx->stream);
     return check_launch(ctx);
 }
 
@@ -414,7 +495,7 @@ int lbm_get_populations(lbm_ctx* ctx, double* f, double* h, double* g) {
     const int nl = ctx->ds.nlat;
     int rc = ensure_stage(ctx, sizeof(double) * 9 * nl * (size_t)n);
     if (rc != LBM_OK) return rc;
-    lbm::launch_get_pops(ctx->kp, ctx->ds, ctx->cur, ctx->stage, ctx->stream);
+    lbm::launch_get_pops(ctx->kp, ctx->ds, fp32_view(ctx), ctx->stage, ctx->stream);
     rc = check_launch(ctx);
     if (rc != LBM_OK) return rc;
     double* out[3] = {f, h, g};
@@ -441,7 +522,11 @@ int lbm_set_populations(lbm_ctx* ctx, const double* f, const double* h, const do
             return cuda_fail(ctx, cudaGetLastError());
         dev[l] = ctx->stage + (size_t)l * 9 * n;
     }
-    lbm::launch_set_pops(ctx->kp, ctx->ds, ctx->cur, dev[0], dev[1], dev[2], ctx->stream);
+    const int b = fp32_view(ctx);
+    lbm::launch_set_pops(ctx->kp, ctx->ds, b, dev[0], dev[1], dev[2], ctx->stream);
+    if (ctx->st != lbm::ST_F32)
+        lbm::launch_pack16(ctx->kp, ctx->pop_alloc[0], ctx->pop16_alloc[ctx->cur], ctx->st,
+                           ctx->stream);
     rc = check_launch(ctx);
     if (rc != LBM_OK) return rc;
     return lbm_synchronize(ctx);
@@ -515,7 +600,8 @@ int lbm_set_launch_shape(lbm_ctx* ctx, int32_t tile_x, int32_t seg_y) {
     if (tile_x < 0 || (tile_x != 0 && (tile_x % 32 != 0 || tile_x < 64 || tile_x > 512)))
         return LBM_ERR_INVALID_ARG;
     if (seg_y != 0 && seg_y < 4) return LBM_ERR_INVALID_ARG;
-    const bool ok_bx = tile_x == 0 || tile_x == 128 || (tile_x == 64 && ctx->kernel == LBM_KERNEL_TMA);
+    const bool ok_bx = tile_x == 0 || tile_x == 128 ||
+                       (tile_x == 64 && ctx->kernel == LBM_KERNEL_TMA && ctx->st == lbm::ST_F32);
     if (!ok_bx) return LBM_ERR_UNSUPPORTED;
     if (tile_x) ctx->shape.bx = tile_x;
     if (seg_y) ctx->shape.seg = seg_y;
@@ -538,11 +624,11 @@ int lbm_save_state(lbm_ctx* ctx, const char* path) {
     if (!ctx || !path) return LBM_ERR_INVALID_ARG;
     int rc = lbm_synchronize(ctx);
     if (rc != LBM_OK) return rc;
-    const size_t pop_n = (size_t)ctx->ds.nlat * 9 * (size_t)ctx->kp.plane;
+    const size_t pop_n = state_words(ctx);
     const size_t vel_n = ctx->kp.coupled ? 0 : 2 * (size_t)ctx->kp.plane;
     float* host = (float*)std::malloc(sizeof(float) * (pop_n + vel_n));
     if (!host) return LBM_ERR_NOMEM;
-    cudaError_t e = cudaMemcpy(host, ctx->pop_alloc[ctx->cur], sizeof(float) * pop_n,
+    cudaError_t e = cudaMemcpy(host, state_alloc(ctx, ctx->cur), sizeof(float) * pop_n,
                                cudaMemcpyDeviceToHost);
     if (e == cudaSuccess && vel_n)
         e = cudaMemcpy(host + pop_n, ctx->fields_alloc + lbm::FP_UX * ctx->kp.plane,
@@ -590,7 +676,7 @@ int lbm_load_state(lbm_ctx* ctx, const char* path) {
         std::fclose(fp);
         return LBM_ERR_IO;
     }
-    const size_t pop_n = (size_t)ctx->ds.nlat * 9 * (size_t)ctx->kp.plane;
+    const size_t pop_n = state_words(ctx);
     const size_t vel_n = ctx->kp.coupled ? 0 : 2 * (size_t)ctx->kp.plane;
     lbm_params mine = ctx->prm, theirs = prm;
     mine.kernel = theirs.kernel = 0;  // the kernel variant does not change the state
@@ -609,7 +695,7 @@ int lbm_load_state(lbm_ctx* ctx, const char* path) {
         std::free(host);
         return LBM_ERR_IO;
     }
-    cudaError_t e = cudaMemcpy(ctx->pop_alloc[ctx->cur], host, sizeof(float) * pop_n,
+    cudaError_t e = cudaMemcpy(state_alloc(ctx, ctx->cur), host, sizeof(float) * pop_n,
                                cudaMemcpyHostToDevice);
     if (e == cudaSuccess && vel_n)
         e = cudaMemcpy(ctx->fields_alloc + lbm::FP_UX * ctx->kp.plane, host + pop_n,
@@ -617,7 +703,8 @@ int lbm_load_state(lbm_ctx* ctx, const char* path) {
     std::free(host);
     if (e != cudaSuccess) return cuda_fail(ctx, e);
     ctx->step = step;
-    return LBM_OK;
+    sync_step_ctr(ctx);
+    return lbm_synchronize(ctx);
 }
 
 }  // extern "C"
@@ -793,6 +880,7 @@ int lbm_batch_create(const lbm_params* params, int32_t nruns, void* stream, lbm_
         if (params[r].mode != params[0].mode) return LBM_ERR_INVALID_ARG;
         if (params[r].kernel != LBM_KERNEL_AUTO && params[r].kernel != LBM_KERNEL_TMA)
             return LBM_ERR_UNSUPPORTED;
+        if (params[r].dtype != LBM_F32) return LBM_ERR_UNSUPPORTED;  // batches store FP32
     }
     if (!lbm::tma_available()) return LBM_ERR_UNSUPPORTED;
     lbm_batch* b = new (std::nothrow) lbm_batch();
@@ -994,7 +1082,7 @@ int lbm_autotune(lbm_ctx* ctx, int32_t steps, int32_t* tile_x, int32_t* seg_y,
     if (ctx->kernel == LBM_KERNEL_SPLIT) return LBM_ERR_UNSUPPORTED;
     int rc = lbm_synchronize(ctx);
     if (rc != LBM_OK) return rc;
-    const size_t pop_bytes = sizeof(float) * (size_t)ctx->ds.nlat * 9 * (size_t)ctx->kp.plane;
+    const size_t pop_bytes = sizeof(float) * state_words(ctx);
     float* snap = nullptr;
     if (cudaMalloc(&snap, pop_bytes) != cudaSuccess) {
         cudaGetLastError();
@@ -1004,17 +1092,18 @@ int lbm_autotune(lbm_ctx* ctx, int32_t steps, int32_t* tile_x, int32_t* seg_y,
     const int64_t step0 = ctx->step;
     const lbm::FusedShape shape0 = ctx->shape;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
-    cudaError_t ce = cudaMemcpy(snap, ctx->pop_alloc[cur0], pop_bytes, cudaMemcpyDeviceToDevice);
+    cudaError_t ce = cudaMemcpy(snap, state_alloc(ctx, cur0), pop_bytes, cudaMemcpyDeviceToDevice);
     if (ce == cudaSuccess) ce = cudaEventCreate(&e0);
     if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
     double best = 1e300;
     lbm::FusedShape best_shape = shape0;
     const int bxs[2] = {128, 64};
-    const int nbx = ctx->kernel == LBM_KERNEL_TMA ? 2 : 1;
+    const int nbx = ctx->kernel == LBM_KERNEL_TMA && ctx->st == lbm::ST_F32 ? 2 : 1;
     for (int a = 0; a < nbx && ce == cudaSuccess && rc == LBM_OK; ++a) {
         const int bx = bxs[a];
-        const int per_sm =
-            ctx->kernel == LBM_KERNEL_TMA ? lbm::tma_blocks_per_sm(bx, ctx->kp.coupled) : 2;
+        const int per_sm = ctx->kernel != LBM_KERNEL_TMA ? 2
+                           : ctx->st != lbm::ST_F32   ? lbm::tma16_blocks_per_sm(ctx->kp.coupled, ctx->st)
+                                                      : lbm::tma_blocks_per_sm(bx, ctx->kp.coupled);
         int segs[8];
         const int ns = seg_candidates(ctx->kp.nx, ctx->kp.ny, bx, per_sm, segs, 8);
         for (int k = 0; k < ns && rc == LBM_OK; ++k) {
@@ -1032,9 +1121,10 @@ int lbm_autotune(lbm_ctx* ctx, int32_t steps, int32_t* tile_x, int32_t* seg_y,
                 best_shape = lbm::FusedShape{bx, segs[k]};
             }
             // put the state back before the next candidate
-            ce = cudaMemcpy(ctx->pop_alloc[cur0], snap, pop_bytes, cudaMemcpyDeviceToDevice);
+            ce = cudaMemcpy(state_alloc(ctx, cur0), snap, pop_bytes, cudaMemcpyDeviceToDevice);
             ctx->cur = cur0;
             ctx->step = step0;
+            sync_step_ctr(ctx);
             if (ce != cudaSuccess) break;
         }
     }

@@ -67,6 +67,13 @@ struct KParams {
     // fixed-point zeroth moments: value = S * fx_inv[l] (l = 0: phi, 1: c)
     float fx_scale[2], fx_inv[2];
     int phi_a_fx, phi_b_fx, phi_m_fx;  // phi_a, phi_b, phi_m in phi fixed point
+    // 16-bit storage: deviations are stored times qs[l] (powers of two;
+    // l = 0: f, 1: h, 2: g), qinv[l] = 1 / qs[l]
+    float qs[3], qinv[3];
+    // 16-bit storage: step counter for the stochastic rounding (device word
+    // holding the step of the launch with step_off 0; see lbm_store16.cuh)
+    const unsigned* step_ctr;
+    int step_off;
     int stall_test;         // test hook: wait on a barrier nothing completes (bounded)
 };
 

@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include "lbm_device.cuh"
+#include "lbm_store16.cuh"
 
 namespace lbm {
 
@@ -54,6 +55,23 @@ void launch_step_tma_batch(const RunDesc* runs, const int4* items, int nitems, i
                            int bx, bool coupled, int src, int* err, cudaStream_t st);
 int tma_batch_blocks_per_sm(int bx, bool coupled);
 int tma_blocks_per_sm(int bx, bool coupled);
+// Fused TMA step with 16-bit storage (lbm_sweep_tma16.cu; block width 128).
+// st: ST_F16 or ST_BF16 (lbm_store16.cuh); buffers hold store_planes(st, .)
+// word planes, pointers to column 0 like the FP32 ones.
+size_t tma16_smem_bytes(bool coupled);
+cudaError_t configure_tma16_smem();
+int tma16_blocks_per_sm(bool coupled, int st);
+void launch_step_tma16(const KParams& p, float* src16, float* dst16, const float* fields,
+                       const FusedShape& sh, const CUtensorMap& map, int st, int* err,
+                       cudaStream_t s);
+// Advance the device step counter of the stochastic rounding by n.
+void launch_step_advance(unsigned* ctr, unsigned n, cudaStream_t s);
+// Whole-buffer conversions between the FP32 deviation-form layout and the
+// 16-bit layout (allocation base pointers; ghost columns included).
+void launch_pack16(const KParams& p, const float* src32_alloc, float* dst16_alloc, int st,
+                   cudaStream_t s);
+void launch_unpack16(const KParams& p, const float* src16_alloc, float* dst32_alloc, int st,
+                     cudaStream_t s);
 // Fill the field planes (phi, c, dP*, sigma, n, |grad phi|) of the current state.
 void launch_fields(const KParams& p, const DevState& s, int src, cudaStream_t st);
 // Macroscopic outputs (float64, dense [ny][nx]) of the current state; needs launch_fields first.
