@@ -175,6 +175,12 @@ int lbm_diagnostics(lbm_ctx *ctx, lbm_diag *out);
  * LBM_ERR_TIMEOUT if a kernel's bounded wait for a staged row expired. */
 int lbm_synchronize(lbm_ctx *ctx);
 
+/* Number of 4-connected components of {phi > level} in the current state
+ * (periodic in x, and in y without walls); a drop that has broken up has
+ * more than one.  Synchronous; uses the context's staging buffer.
+ * Errors: INVALID_ARG, NOMEM, CUDA. */
+int lbm_count_components(lbm_ctx *ctx, double level, int32_t *count);
+
 /* Steps taken since the last initialisation (-1 for a NULL context). */
 int64_t lbm_get_step(const lbm_ctx *ctx);
 
@@ -267,6 +273,44 @@ int lbm_batch_get_launch_shape(const lbm_batch *b, int32_t *tile_x, int32_t *seg
  * (one snapshot buffer per run while it runs).  Synchronous. */
 int lbm_batch_autotune(lbm_batch *b, int32_t steps, int32_t *tile_x, int32_t *seg_y,
                        double *ms_per_step);
+
+/* ------------------------------------------------------------------------
+ * Surrogate network (the learned part that picks capillary numbers near
+ * drop breakup; not in the paper).  A multilayer perceptron with 5 inputs,
+ * four hidden layers of width 128 with SiLU, and 2 outputs (steady
+ * deformation D and a breakup logit); BF16 weights, FP32 accumulation, FP32
+ * master weights trained with Adam (beta1 0.9, beta2 0.999, eps 1e-8).
+ * Loss: mean((D - yD)^2) + mean(BCE(logit, yB)).
+ *
+ * Parameters form one FP32 vector of surr_param_count() values: for each
+ * layer l = 0..4 (fan-in WIDTH[l], fan-out WIDTH[l+1], WIDTH = 5, 128, 128,
+ * 128, 128, 2) the weights W[fout][fin] row-major, then the biases b[fout].
+ * The forward and backward passes use the weights rounded to BF16 (nearest,
+ * ties to even); biases stay FP32.
+ *
+ * Host arrays: X [n][5] float32 row-major; yD, yB, D_out, logit_out [n].
+ * All calls are synchronous on the context's stream (NULL: legacy default).
+ * Errors: INVALID_ARG, NOMEM, CUDA. */
+typedef struct surr_ctx surr_ctx;
+int32_t surr_param_count(void);
+/* Create with He-initialised weights (N(0, 2/fan_in) from a SplitMix64 /
+ * Box-Muller stream seeded by `seed`) and zero biases. */
+int surr_create(uint64_t seed, void *stream, surr_ctx **out);
+void surr_destroy(surr_ctx *ctx);
+/* Replace / read the FP32 master parameters (set also resets Adam). */
+int surr_set_params(surr_ctx *ctx, const float *params);
+int surr_get_params(surr_ctx *ctx, float *params);
+/* Outputs for n samples. */
+int surr_predict(surr_ctx *ctx, const float *X, int32_t n, float *D_out, float *logit_out);
+/* Gradient of the loss over n samples with respect to every parameter (same
+ * layout as the parameters; NULL to skip) and the loss (NULL to skip);
+ * parameters unchanged. */
+int surr_grad(surr_ctx *ctx, const float *X, const float *yD, const float *yB, int32_t n,
+              float *grads, double *loss);
+/* `epochs` full-batch Adam steps on the n samples with learning rate lr;
+ * loss_out (nullable): loss after the last step. */
+int surr_train(surr_ctx *ctx, const float *X, const float *yD, const float *yB, int32_t n,
+               int32_t epochs, float lr, double *loss_out);
 
 /* ------------------------------------------------------------------------
  * Field statistics without allocation.  The paper has no counterpart: this

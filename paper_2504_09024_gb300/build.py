@@ -16,7 +16,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "_lib")
 SO = os.path.join(LIBDIR, "liblbm.so")
-SOURCES = ["lbm_kernels.cu", "lbm_sweep_tma.cu", "lbm_sweep_tma16.cu", "lbm_api.cu", "lbm_noalloc.cu"]
+SOURCES = ["lbm_kernels.cu", "lbm_sweep_tma.cu", "lbm_sweep_tma16.cu", "lbm_api.cu", "lbm_noalloc.cu",
+           "surr_mlp.cu"]
 HEADERS = ["lbm_device.cuh", "lbm_internal.h", "lbm_cell.cuh", "lbm_tma.cuh", "lbm_sweep_tile.cuh",
            "lbm_store16.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -566,6 +566,42 @@ int lbm_diagnostics(lbm_ctx* ctx, lbm_diag* out) {
     return LBM_OK;
 }
 
+int lbm_count_components(lbm_ctx* ctx, double level, int32_t* count) {
+    if (!ctx || !count) return LBM_ERR_INVALID_ARG;
+    const int64_t n = cells(ctx);
+    // labels and flags live in the staging buffer (int32 per cell, then 2 ints)
+    int rc = ensure_stage(ctx, sizeof(int) * (size_t)(n + 2) + sizeof(double));
+    if (rc != LBM_OK) return rc;
+    int* label = reinterpret_cast<int*>(ctx->stage);
+    int* flag = label + n;  // [0]: changed, [1]: root count
+    const int b = fp32_view(ctx);
+    lbm::launch_fields(ctx->kp, ctx->ds, b, ctx->stream);
+    lbm::launch_label_init(ctx->kp, ctx->ds.fields, (float)level, label, ctx->stream);
+    // each sweep moves every label at least one cell and halves pointer
+    // chains, so n sweeps always suffice
+    for (int64_t it = 0; it < n + 1; ++it) {
+        int changed = 0;
+        cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(int), ctx->stream);
+        if (e == cudaSuccess) {
+            lbm::launch_label_step(ctx->kp, label, flag, ctx->stream);
+            e = cudaMemcpyAsync(&changed, flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, e);
+        if (!changed) break;
+    }
+    int roots = 0;
+    cudaError_t e = cudaMemsetAsync(flag + 1, 0, sizeof(int), ctx->stream);
+    if (e == cudaSuccess) {
+        lbm::launch_label_roots(ctx->kp, label, flag + 1, ctx->stream);
+        e = cudaMemcpyAsync(&roots, flag + 1, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e);
+    *count = roots;
+    return lbm_synchronize(ctx);
+}
+
 int lbm_synchronize(lbm_ctx* ctx) {
     if (!ctx) return LBM_ERR_INVALID_ARG;
     cudaError_t e = cudaStreamSynchronize(ctx->stream);

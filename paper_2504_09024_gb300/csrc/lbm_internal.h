@@ -88,6 +88,13 @@ void launch_get_pops(const KParams& p, const DevState& s, int src, double* out, 
 void launch_set_pops(const KParams& p, const DevState& s, int dst, const double* f,
                      const double* h, const double* g, cudaStream_t st);
 
+// Connected components of {phi > level} (4-neighbour, periodic in x, and in
+// y without walls) on the FP_PHI field plane: label init, one propagation
+// sweep (sets *changed when a label moved), root count.
+void launch_label_init(const KParams& p, const float* fields, float level, int* label,
+                       cudaStream_t st);
+void launch_label_step(const KParams& p, int* label, int* changed, cudaStream_t st);
+void launch_label_roots(const KParams& p, const int* label, int* count, cudaStream_t st);
 // FP64 reductions: partial sums per block into `partial`, then a fixed-order finish.
 constexpr int DIAG_NSUM = 12;
 int diag_blocks(const KParams& p);

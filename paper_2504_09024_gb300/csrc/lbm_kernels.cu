@@ -727,4 +727,67 @@ void launch_diag(const KParams& p, const double* phi, const double* c, const dou
     k_diag_finish2<<<1, 32, 0, st>>>(partial, nb, result);
 }
 
+// ---------------------------------------------------------------------------
+// 4-connected components of {phi > level}: labels by minimum-index
+// propagation with pointer jumping (the label of a cell is the smallest cell
+// index reachable inside the set), then a count of the roots.
+// ---------------------------------------------------------------------------
+
+__global__ void k_label_init(const KParams p, const float* __restrict__ F, float level,
+                             int* __restrict__ label) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= (int64_t)p.nx * p.ny) return;
+    const int i = (int)(k % p.nx), j = (int)(k / p.nx);
+    // the phi plane holds the fixed-point zeroth moment
+    const int phi_fx = __float_as_int(F[FP_PHI * p.plane + (int64_t)j * p.pitch + i]);
+    label[k] = (phi_fx != FX_INVALID && (float)phi_fx * p.fx_inv[0] > level) ? (int)k : -1;
+}
+
+__global__ void k_label_step(const KParams p, int* __restrict__ label, int* __restrict__ changed) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= (int64_t)p.nx * p.ny) return;
+    const int own = label[k];
+    if (own < 0) return;
+    const int i = (int)(k % p.nx), j = (int)(k / p.nx);
+    int m = own;
+    const int nb[4][2] = {{wrap_i(i - 1, p.nx), j}, {wrap_i(i + 1, p.nx), j}, {i, j - 1}, {i, j + 1}};
+#pragma unroll
+    for (int d = 0; d < 4; ++d) {
+        int jj = nb[d][1];
+        if (jj < 0 || jj >= p.ny) {
+            if (p.walls) continue;  // no neighbour across a wall
+            jj = wrap_i(jj, p.ny);
+        }
+        const int v = label[(int64_t)jj * p.nx + nb[d][0]];
+        if (v >= 0 && v < m) m = v;
+    }
+    m = min(m, label[m]);  // pointer jumping
+    if (m < own) {
+        atomicMin(&label[k], m);
+        *changed = 1;
+    }
+}
+
+__global__ void k_label_roots(const KParams p, const int* __restrict__ label, int* __restrict__ count) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= (int64_t)p.nx * p.ny) return;
+    if (label[k] == (int)k) atomicAdd(count, 1);
+}
+
+void launch_label_init(const KParams& p, const float* fields, float level, int* label,
+                       cudaStream_t st) {
+    const int64_t n = (int64_t)p.nx * p.ny;
+    k_label_init<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(p, fields, level, label);
+}
+
+void launch_label_step(const KParams& p, int* label, int* changed, cudaStream_t st) {
+    const int64_t n = (int64_t)p.nx * p.ny;
+    k_label_step<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(p, label, changed);
+}
+
+void launch_label_roots(const KParams& p, const int* label, int* count, cudaStream_t st) {
+    const int64_t n = (int64_t)p.nx * p.ny;
+    k_label_roots<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(p, label, count);
+}
+
 }  // namespace lbm

@@ -102,7 +102,18 @@ SIGNATURES = {
     "lbm_batch_autotune": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
                                           ctypes.POINTER(ctypes.c_int32),
                                           ctypes.POINTER(ctypes.c_double)]),
+    "lbm_count_components": (ctypes.c_int, [_VP, ctypes.c_double, ctypes.POINTER(ctypes.c_int32)]),
     "lbm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "surr_param_count": (ctypes.c_int32, []),
+    "surr_create": (ctypes.c_int, [ctypes.c_uint64, _VP, ctypes.POINTER(_VP)]),
+    "surr_destroy": (None, [_VP]),
+    "surr_set_params": (ctypes.c_int, [_VP, _DP]),
+    "surr_get_params": (ctypes.c_int, [_VP, _DP]),
+    "surr_predict": (ctypes.c_int, [_VP, _DP, ctypes.c_int32, _DP, _DP]),
+    "surr_grad": (ctypes.c_int, [_VP, _DP, _DP, _DP, ctypes.c_int32, _DP,
+                                 ctypes.POINTER(ctypes.c_double)]),
+    "surr_train": (ctypes.c_int, [_VP, _DP, _DP, _DP, ctypes.c_int32, ctypes.c_int32,
+                                  ctypes.c_float, ctypes.POINTER(ctypes.c_double)]),
 }
 
 LBM_FIELD_STATS_LEN = 13
@@ -325,6 +336,12 @@ def lbm_batch_autotune(b, steps=16):
     return tx.value, sy.value, ms.value
 
 
+def lbm_count_components(ctx, level=0.5) -> int:
+    n = ctypes.c_int32()
+    _check(load().lbm_count_components(ctx, float(level), ctypes.byref(n)), "lbm_count_components")
+    return n.value
+
+
 def lbm_strerror(code: int) -> str:
     return load().lbm_strerror(code).decode()
 
@@ -409,6 +426,9 @@ class Sim:
     def set_launch_shape(self, tile_x=0, seg_y=0):
         lbm_set_launch_shape(self.ctx, tile_x, seg_y)
 
+    def components(self, level=0.5):
+        return lbm_count_components(self.ctx, level)
+
     def save(self, path):
         lbm_save_state(self.ctx, path)
 
@@ -456,3 +476,89 @@ class Batch:
 
     def autotune(self, steps=16):
         return lbm_batch_autotune(self.handle, steps)
+
+
+# --- surrogate network -------------------------------------------------------
+
+SURR_WIDTHS = (5, 128, 128, 128, 128, 2)
+
+
+def _f32(a, shape=None):
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    if shape is not None and a.shape != shape:
+        raise ValueError(f"expected shape {shape}, got {a.shape}")
+    return a
+
+
+class Surrogate:
+    """The surrogate network of liblbm.so (all arithmetic in its kernels).
+    Parameters travel as a list of (W [fout, fin], b [fout]) float32 pairs."""
+
+    def __init__(self, seed=0, stream=None):
+        out = _VP()
+        _check(load().surr_create(int(seed), stream, ctypes.byref(out)), "surr_create")
+        self.h = out.value
+        self.count = int(load().surr_param_count())
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().surr_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def flatten(params):
+        return np.concatenate([np.concatenate([np.asarray(W, np.float32).ravel(),
+                                               np.asarray(b, np.float32).ravel()])
+                               for W, b in params])
+
+    @staticmethod
+    def unflatten(flat):
+        out, o = [], 0
+        for fin, fout in zip(SURR_WIDTHS[:-1], SURR_WIDTHS[1:]):
+            W = flat[o:o + fout * fin].reshape(fout, fin)
+            o += fout * fin
+            b = flat[o:o + fout]
+            o += fout
+            out.append([W.copy(), b.copy()])
+        return out
+
+    def set_params(self, params):
+        flat = _f32(self.flatten(params))
+        assert flat.size == self.count
+        _check(load().surr_set_params(self.h, flat.ctypes.data), "surr_set_params")
+
+    def get_params(self):
+        flat = np.empty(self.count, np.float32)
+        _check(load().surr_get_params(self.h, flat.ctypes.data), "surr_get_params")
+        return self.unflatten(flat)
+
+    def predict(self, X):
+        X = _f32(X)
+        n = X.shape[0]
+        D = np.empty(n, np.float32)
+        z = np.empty(n, np.float32)
+        _check(load().surr_predict(self.h, X.ctypes.data, n, D.ctypes.data, z.ctypes.data),
+               "surr_predict")
+        return D, z
+
+    def grad(self, X, yD, yB):
+        X, yD, yB = _f32(X), _f32(yD), _f32(yB)
+        g = np.empty(self.count, np.float32)
+        loss = ctypes.c_double()
+        _check(load().surr_grad(self.h, X.ctypes.data, yD.ctypes.data, yB.ctypes.data,
+                                X.shape[0], g.ctypes.data, ctypes.byref(loss)), "surr_grad")
+        return self.unflatten(g), loss.value
+
+    def train(self, X, yD, yB, epochs, lr):
+        X, yD, yB = _f32(X), _f32(yD), _f32(yB)
+        loss = ctypes.c_double()
+        _check(load().surr_train(self.h, X.ctypes.data, yD.ctypes.data, yB.ctypes.data,
+                                 X.shape[0], int(epochs), float(lr), ctypes.byref(loss)),
+               "surr_train")
+        return loss.value

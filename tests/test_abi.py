@@ -25,14 +25,14 @@ def lib():
 def declared_functions():
     text = open(HEADER).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(lbm_[a-z_]+)\s*\(", text)))
+    return sorted(set(re.findall(r"\b((?:lbm|surr)_[a-z_]+)\s*\(", text)))
 
 
 def test_header_functions_exported(lib):
     names = declared_functions()
     assert len(names) >= 20
     out = subprocess.run(["nm", "-D", "--defined-only", B.SO], capture_output=True, text=True).stdout
-    exported = set(re.findall(r"\bT (lbm_\w+)", out))
+    exported = set(re.findall(r"\bT ((?:lbm|surr)_\w+)", out))
     missing = [n for n in names if n not in exported]
     assert not missing, missing
     assert sorted(lbm.SIGNATURES) == names

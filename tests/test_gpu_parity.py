@@ -260,3 +260,49 @@ def test_nonfinite_reported():
     s.init(phi, case.c, case.ux, case.uy)
     d = s.diagnostics()
     assert d["nonfinite"] > 0 and d["status"] == lbm.LBM_ERR_NONFINITE
+
+
+def _components_reference(mask, periodic_y):
+    """4-connected components of a boolean mask, periodic in x (and y)."""
+    from scipy import ndimage
+    lab, n = ndimage.label(mask)
+    parent = list(range(n + 1))
+
+    def find(a):
+        while parent[a] != a:
+            parent[a] = parent[parent[a]]
+            a = parent[a]
+        return a
+
+    pairs = [(lab[:, 0], lab[:, -1])]
+    if periodic_y:
+        pairs.append((lab[0, :], lab[-1, :]))
+    for a, b in pairs:
+        for u, v in zip(a, b):
+            if u and v:
+                parent[find(u)] = find(v)
+    return len({find(k) for k in range(1, n + 1)})
+
+
+@pytest.mark.parametrize("walls", [0, 1])
+def test_count_components(walls):
+    nx, ny = 160, 72
+    X, Y = W.cell_centres(nx, ny)
+    phys = W.Physics(nx=nx, ny=ny, walls_y=walls, mode=0)
+    layouts = {
+        "one": [(80.0, 36.0, 14.0)],
+        "two": [(40.0, 36.0, 12.0), (115.0, 36.0, 12.0)],
+        "wrap_x": [(2.0, 36.0, 12.0)],
+        "three": [(30.0, 20.0, 8.0), (80.0, 50.0, 9.0), (130.0, 30.0, 10.0)],
+    }
+    for name, drops in layouts.items():
+        phi = np.zeros((ny, nx))
+        for xc, yc, R in drops:
+            dx = np.minimum(np.abs(X - xc), nx - np.abs(X - xc))
+            r = np.hypot(dx, Y - yc)
+            phi = np.maximum(phi, 0.5 * (1 + np.tanh(2 * (R - r) / 4.0)))
+        s = lbm.Sim(phys)
+        s.init(phi, 0.1 * phi, np.zeros_like(phi), np.zeros_like(phi))
+        got = s.components(0.5)
+        ref = _components_reference(s.fields()["phi"] > 0.5, periodic_y=not walls)
+        assert got == ref == len(drops), (name, got, ref)
