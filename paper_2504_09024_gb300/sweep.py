@@ -13,11 +13,12 @@ lattice step, diagnostic, component count and network step runs in the
 library's CUDA kernels (lbm.Batch, lbm.Surrogate).
 
 Run definition (all runs share one grid so that they step together):
-  grid nx x ny (default 256 x 128), R = H / 5, W = 4, Re = 1, nu = 0.1,
-  u(y) = U0 (2y/H - 1) between walls moving at -+U0, density and viscosity
-  ratio 1; t* = gamma_dot t = 20.  Labels: D = mean of 5 samples over the
-  last 10% of the run, breakup = more than one connected component of
-  phi > 1/2 at the end (or a non-finite state).
+  grid nx x ny (default 384 x 128, nx = 3 H), R = H / 8 (2R/H = 0.25), W = 4,
+  Re = 1, nu = 0.1, u(y) = U0 (2y/H - 1) between walls moving at -+U0,
+  density and viscosity ratio 1; t* = gamma_dot t = 25 (the breakup
+  sequence of Sec. 4.4 at Re = 1 runs to t* = 25).  Labels: D = mean of 5
+  samples over the last 10% of the run, breakup = more than one connected
+  component of phi > 1/2 at the end (or a non-finite state).
 """
 from __future__ import annotations
 
@@ -33,20 +34,21 @@ from . import lbm, workloads as W
 CA_RANGE = (0.05, 0.5)
 RE = 1.0
 NU = 0.1
-T_STAR = 20.0
+T_STAR = 25.0
+R_OVER_H = 1.0 / 8.0
 BRACKET = 0.05          # the LBM checks Ca_pred -+ BRACKET
 
 
 def draw_points(n, seed):
     """Sweep / training points: Ca ~ U[0.05, 0.5], beta ~ U[0, 0.5],
-    Pe_s ~ logU[1, 100], Gamma0 ~ U[0.1, 0.6], 2R/H = 0.4 (R = H / 5)."""
+    Pe_s ~ logU[1, 100], Gamma0 ~ U[0.1, 0.6], 2R/H = 0.25 (R = H / 8)."""
     rng = np.random.default_rng(seed)
     return {
         "Ca": rng.uniform(*CA_RANGE, n),
         "beta": rng.uniform(0.0, 0.5, n),
         "Pe_s": np.exp(rng.uniform(0.0, math.log(100.0), n)),
         "Gamma0": rng.uniform(0.1, 0.6, n),
-        "aspect": np.full(n, 0.4),
+        "aspect": np.full(n, 2.0 * R_OVER_H),
     }
 
 
@@ -56,7 +58,7 @@ def features(pts):
                      (np.asarray(pts["beta"]) - 0.25) / 0.25,
                      np.log10(np.asarray(pts["Pe_s"])) - 1.0,
                      (np.asarray(pts["Gamma0"]) - 0.35) / 0.25,
-                     (np.asarray(pts["aspect"]) - 0.4) / 0.1], axis=1).astype(np.float32)
+                     (np.asarray(pts["aspect"]) - 0.25) / 0.1], axis=1).astype(np.float32)
 
 
 def subset(pts, idx):
@@ -65,13 +67,13 @@ def subset(pts, idx):
 
 def make_case(Ca, beta, Pe_s, Gamma0, grid):
     nx, ny = grid
-    return W.shear_drop(nx, ny, ny / 5.0, 4.0, Ca=float(Ca), beta=float(beta),
+    return W.shear_drop(nx, ny, ny * R_OVER_H, 4.0, Ca=float(Ca), beta=float(beta),
                         Gamma0=float(Gamma0), Re=RE, Pe_s=float(Pe_s), nu=NU,
                         name=f"sweep_{nx}x{ny}")
 
 
 def run_steps(grid, t_star=T_STAR):
-    gamma_dot = RE * NU / (grid[1] / 5.0) ** 2
+    gamma_dot = RE * NU / (grid[1] * R_OVER_H) ** 2
     return int(math.ceil(t_star / gamma_dot / 32.0)) * 32
 
 
@@ -103,7 +105,7 @@ def lbm_labels(pts, grid, t_star=T_STAR, batch=512, samples=5):
                 d = r.diagnostics()
                 hist[j, m] = d["D"]
                 bad[j] |= d["nonfinite"] > 0
-        gd = RE * NU / (grid[1] / 5.0) ** 2
+        gd = RE * NU / (grid[1] * R_OVER_H) ** 2
         tm = np.asarray(marks, dtype=float) * gd
         for j, r in enumerate(b.runs):
             k = idx[j]
@@ -194,7 +196,7 @@ def lbm_bisection(pts, grid, width=2 * BRACKET, t_star=T_STAR, batch=512):
 
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
-    ap.add_argument("--grid", default="256x128")
+    ap.add_argument("--grid", default="384x128")
     ap.add_argument("--train", type=int, default=1024)
     ap.add_argument("--points", type=int, default=256)
     ap.add_argument("--baseline-points", type=int, default=64)

@@ -25,7 +25,7 @@ def test_bisection_finds_a_known_boundary():
 
 
 def test_sweep_pipeline_small():
-    rep = sweep.main(["--grid", "64x32", "--train", "48", "--points", "8",
+    rep = sweep.main(["--grid", "96x32", "--train", "48", "--points", "8",
                       "--baseline-points", "4", "--t-star", "0.3", "--epochs", "300"])
     assert rep["train_runs"] == 48 and rep["sweep_points"] == 8
     assert rep["verify_runs"] == 2 * rep["predicted"]
