@@ -319,20 +319,22 @@ __device__ __forceinline__ float iso_div(const float vx[3][3], const float vy[3]
 }
 
 __device__ __forceinline__ void unit_normal(float gx, float gy, float& nx, float& ny, float& mag) {
-    mag = sqrtf(gx * gx + gy * gy);
-    if (mag > EPS_N) {
-        float inv = 1.0f / mag;
+    const float g2 = gx * gx + gy * gy;
+    if (g2 > EPS_N * EPS_N) {
+        const float inv = rsqrtf(g2);  // within 2 ulp; n and |grad phi| to ~1e-7
         nx = gx * inv;
         ny = gy * inv;
+        mag = g2 * inv;
     } else {
         nx = 0.0f;
         ny = 0.0f;
+        mag = sqrtf(g2);
     }
 }
 
 // Langmuir isotherm, Eq. (EOS).
 __device__ __forceinline__ float sigma_of_c(const KParams& p, float c) {
-    return p.sigma_o * (1.0f + p.beta * logf(1.0f - c * p.inv_cmax));
+    return p.sigma_o * (1.0f + p.beta * __logf(1.0f - c * p.inv_cmax));
 }
 
 // ---------------------------------------------------------------------------

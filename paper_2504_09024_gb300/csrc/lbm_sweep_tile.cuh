@@ -365,12 +365,12 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap* tmap, const KParam
                         store9(dst + 18 * p.plane, p, idx, i, gg);
                     } else {
                         const float sg = p.qs[2];
-                        const uint32_t seed = pcg_hash(step_seed ^ (uint32_t)(jc * p.nx + i));
+                        const uint32_t seed = pcg_hash(step_seed ^ (uint32_t)(jc * p.nx + i) ^ 0x80000000u);
                         uint32_t w[5];
 #pragma unroll
                         for (int k = 0; k < 5; ++k)
                             w[k] = pack2_sr<ST>(gg[2 * k] * sg, 2 * k + 1 < 9 ? gg[2 * k + 1] * sg : 0.0f,
-                                                pcg_hash(seed + 10u + (uint32_t)k));
+                                                word_bits(seed, 9 + k));
                         const int gs[2] = {ghost_right(p, i), ghost_left(p, i)};
                         store_words<5>(dst, p.plane, idx, gs, P16_G, w);
                     }
@@ -409,7 +409,7 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap* tmap, const KParam
                         w[0] = (uint32_t)phi_fx;
                         w[1] = __float_as_uint(ks[3][2]);
 #pragma unroll
-                        for (int q = 1; q < 9; ++q) w[1 + q] = pack2_sr<ST>(df[q] * sf, dh[q] * sh, pcg_hash(seed + (uint32_t)q));
+                        for (int q = 1; q < 9; ++q) w[1 + q] = pack2_sr<ST>(df[q] * sf, dh[q] * sh, word_bits(seed, q));
                         const int gs[2] = {ghost_right(p, i), ghost_left(p, i)};
                         store_words<10>(dst, p.plane, idx, gs, 0, w);
                     }
