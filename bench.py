@@ -98,6 +98,21 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
+def max_over_ranks(x, dist=None, device="cuda"):
+    """The largest value of x over all ranks (x itself on one rank)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mlups(world, cells_per_rank, steps, seconds):
+    """Cell updates of all ranks per second of the slowest rank, in millions."""
+    return world * cells_per_rank * steps / seconds / 1e6
+
+
 def make_case(name):
     from paper_2504_09024_gb300 import workloads as W
     if name == "2048x1024":
@@ -256,12 +271,9 @@ def run_ensemble(args, rank, world, local_rank):
     if dist is not None:
         dist.barrier()
     clk = clocks.stop()
-    t = torch.tensor([e0.elapsed_time(e1)], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max = max_over_ranks(e0.elapsed_time(e1), dist)
     ms_step = ms_max / args.steps
-    value = world * ncell * args.steps / (ms_max * 1e-3) / 1e6
+    value = whole_job_mlups(world, ncell, args.steps, ms_max * 1e-3)
 
     # end to end through the public API: every run initialised from pinned
     # host fields, K batched steps, every run's fields read back + diagnostics
@@ -280,10 +292,7 @@ def run_ensemble(args, rank, world, local_rank):
         diags.append(r.diagnostics())
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    e2e_s = float(t.item())
+    e2e_s = max_over_ranks(e2e_s, dist)
     h2d = sum(a.numel() * 8 for h in host_in for a in h)
     d2h = sum(a.numel() * 8 for h in host_out for a in h) + 128 * len(cases)
 
@@ -309,7 +318,7 @@ def run_ensemble(args, rank, world, local_rank):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_kind": f"{peak_kind} hbm_gbs",
                      "bytes_per_cell": bpc, "traffic": None},
-        "e2e": {"value": world * ncell * args.steps / e2e_s / 1e6, "unit": UNIT,
+        "e2e": {"value": whole_job_mlups(world, ncell, args.steps, e2e_s), "unit": UNIT,
                 "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
                 "what": "lbm_init_fields of every run from pinned host fields + "
                         "lbm_batch_step(K) + lbm_get_fields and lbm_diagnostics of every run"},
@@ -377,12 +386,8 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     barrier()
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1)
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = world * ncell * args.steps / (ms_max * 1e-3) / 1e6
+    ms_max = max_over_ranks(e0.elapsed_time(e1), dist)
+    value = whole_job_mlups(world, ncell, args.steps, ms_max * 1e-3)
     ms_step = ms_max / args.steps
 
     # end-to-end through the public API with pinned host buffers: initialise
@@ -399,10 +404,7 @@ def run_ours(args, rank, world, local_rank):
     diag = sim.diagnostics()
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    e2e_s = float(t.item())
+    e2e_s = max_over_ranks(e2e_s, dist)
     h2d = sum(a.numel() * 8 for a in host_in)
     d2h = sum(a.numel() * 8 for a in host_out) + 128
 
@@ -428,7 +430,7 @@ def run_ours(args, rank, world, local_rank):
                      "frac": achieved / peak, "peak_kind": f"{peak_kind} hbm_gbs",
                      "bytes_per_cell": bpc,
                      "traffic": tr["bytes_per_launch"] if tr else None},
-        "e2e": {"value": world * ncell * args.steps / e2e_s / 1e6, "unit": UNIT,
+        "e2e": {"value": whole_job_mlups(world, ncell, args.steps, e2e_s), "unit": UNIT,
                 "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
                 "what": "lbm_init_fields from pinned host fields + lbm_step(K) + lbm_get_fields "
                         "to pinned host + lbm_diagnostics"},
