@@ -476,6 +476,12 @@ __device__ __forceinline__ void collide_flow(float a[9], const FlowMacro& m, flo
     k[8] = -R * (ux2 * uy2 + CS2 * (ux2 + uy2)) + dP * (ux2 + CS2) * (uy2 + CS2);
     float r[9];
     central_to_raw(k, ux, uy, r);
+    // The raw first moments of the post-collision state are exactly
+    // rho cs2 u + cs2 F_t / 2; formed directly they carry one rounding
+    // instead of the FP32 cancellation of u (P - P0 + G/2) + u (rho cs2 - P + P0).
+    // Explicit FMAs: every kernel that inlines this rounds it the same way.
+    r[1] = __fmaf_rn(R, ux, __fmul_rn(0.5f * CS2, m.Ftx));
+    r[2] = __fmaf_rn(R, uy, __fmul_rn(0.5f * CS2, m.Fty));
     raw_to_pops(r, a);
 }
 

@@ -153,6 +153,7 @@ def test_precision_2048x1024_5000_steps(Ca):
     ref = o.fields()
     d_ref = o.diagnostics()
     bounds = {lbm.LBM_F32: TOL, **BOUND}
+    failed = []
     for dtype, bound in bounds.items():
         s = lbm.Sim(case.phys, dtype=dtype)
         s.init(case.phi, case.c, case.ux, case.uy)
@@ -165,4 +166,6 @@ def test_precision_2048x1024_5000_steps(Ca):
               f"{(d1['sum_phi'] - d0['sum_phi']) / d0['sum_phi']:.2e}  sum_c drift "
               f"{(d1['sum_c'] - d0['sum_c']) / d0['sum_c']:.2e}  D {d1['D']:.6f} (oracle "
               f"{d_ref['D']:.6f})")
-        assert max(e.values()) <= bound, (dtype, e)
+        if max(e.values()) > bound:
+            failed.append((dtype, e))
+    assert not failed, failed
