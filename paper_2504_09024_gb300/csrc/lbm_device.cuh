@@ -343,15 +343,18 @@ __device__ __forceinline__ float sigma_of_c(const KParams& p, float c) {
 
 // P^-1 applied to raw moments r = (00,10,01,20,02,11,21,12,22) (App. A).
 __device__ __forceinline__ void raw_to_pops(const float r[9], float out[9]) {
-    out[0] = r[0] - r[3] - r[4] + r[8];
-    out[1] = 0.5f * (r[1] + r[3] - r[7] - r[8]);
-    out[2] = 0.5f * (r[2] + r[4] - r[6] - r[8]);
-    out[3] = 0.5f * (-r[1] + r[3] + r[7] - r[8]);
-    out[4] = 0.5f * (-r[2] + r[4] + r[6] - r[8]);
-    out[5] = 0.25f * (r[5] + r[6] + r[7] + r[8]);
-    out[6] = 0.25f * (-r[5] + r[6] - r[7] + r[8]);
-    out[7] = 0.25f * (r[5] - r[6] - r[7] + r[8]);
-    out[8] = 0.25f * (-r[5] - r[6] + r[7] + r[8]);
+    // factored: the eight pair sums and differences are shared by two outputs each
+    const float a = r[3] - r[8], b = r[1] - r[7], c = r[4] - r[8], d = r[2] - r[6];
+    const float e = r[8] + r[5], f = r[6] + r[7], g = r[8] - r[5], h = r[6] - r[7];
+    out[0] = (r[0] - r[3]) - c;
+    out[1] = 0.5f * (a + b);
+    out[2] = 0.5f * (c + d);
+    out[3] = 0.5f * (a - b);
+    out[4] = 0.5f * (c - d);
+    out[5] = 0.25f * (e + f);
+    out[6] = 0.25f * (g + h);
+    out[7] = 0.25f * (e - f);
+    out[8] = 0.25f * (g - h);
 }
 
 // F^-1(u) applied to central moments k (binomial expansion of ((e-u)+u)^m).
@@ -477,11 +480,14 @@ __device__ __forceinline__ void collide_flow(float a[9], const FlowMacro& m, flo
     float r[9];
     central_to_raw(k, ux, uy, r);
     // The raw first moments of the post-collision state are exactly
-    // rho cs2 u + cs2 F_t / 2; formed directly they carry one rounding
-    // instead of the FP32 cancellation of u (P - P0 + G/2) + u (rho cs2 - P + P0).
+    // rho cs2 u + cs2 F_t / 2 = j + cs2 F_t (j: pre-collision momentum, with
+    // rho cs2 u = j + cs2 F_t / 2).  Formed from j they carry the momentum
+    // forward without passing through the rounded u: re-forming it from u
+    // every step adds the rounding of u to the momentum, and for a slowly
+    // varying flow that rounding repeats step after step and accumulates.
     // Explicit FMAs: every kernel that inlines this rounds it the same way.
-    r[1] = __fmaf_rn(R, ux, __fmul_rn(0.5f * CS2, m.Ftx));
-    r[2] = __fmaf_rn(R, uy, __fmul_rn(0.5f * CS2, m.Fty));
+    r[1] = __fmaf_rn(CS2, m.Ftx, jx);
+    r[2] = __fmaf_rn(CS2, m.Fty, jy);
     raw_to_pops(r, a);
 }
 

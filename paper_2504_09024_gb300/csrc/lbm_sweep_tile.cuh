@@ -392,8 +392,9 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap* tmap, const KParam
                         ux = s_ux[(jc & 1) * BX + t];
                         uy = s_uy[(jc & 1) * BX + t];
                     } else {
-                        ux = F[FP_UX * p.plane + idx];
-                        uy = F[FP_UY * p.plane + idx];
+                        const int64_t fi = idx;
+                        ux = F[FP_UX * p.plane + fi];
+                        uy = F[FP_UY * p.plane + fi];
                     }
                     float df[9], dh[9];
                     collide_scalars_cell(p, phi_fx, (float)phi_fx * p.fx_inv[0], s_c[c0 * BX + t],
