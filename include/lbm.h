@@ -228,10 +228,12 @@ int lbm_autotune(lbm_ctx *ctx, int32_t steps, int32_t *tile_x, int32_t *seg_y,
 
 /* ------------------------------------------------------------------------
  * Batches (ensembles of independent runs, e.g. drops in shear at different
- * grid sizes and parameters).  A batch owns one context per run; every
- * batched step advances all runs by one persistent launch of the TMA sweep
- * kernel that walks a list of tiles over all runs (larger runs first), and
- * step loops are replayed from captured CUDA graphs.  Runs are independent:
+ * grid sizes and parameters).  A batch owns one context per run.  Step
+ * loops are replayed from captured CUDA graphs of 32 steps that hold one
+ * chain of TMA sweep launches per run, the chains spread over up to 16 side
+ * streams and run concurrently; a remainder of fewer than 32 steps advances
+ * all runs by one persistent launch of the same sweep that walks a list of
+ * tiles over all runs (larger runs first).  Runs are independent:
  * each follows Sec. 3 and App. C-D exactly as a single context does, and a
  * batched step gives results identical to stepping each run's context on its
  * own with the same launch shape.
@@ -270,7 +272,9 @@ int lbm_batch_get_launch_shape(const lbm_batch *b, int32_t *tile_x, int32_t *seg
 
 /* Autotuner of the batched launch shape: tile_x in {128, 64} x seg_y in
  * {16, 24, 32, 48, 64, 96, 128}, timed and restored as in lbm_autotune
- * (one snapshot buffer per run while it runs).  Synchronous. */
+ * (one snapshot buffer per run while it runs).  Each shape is timed on
+ * `steps` rounded up to whole 32-step graphs, after one graph of warm-up.
+ * Synchronous. */
 int lbm_batch_autotune(lbm_batch *b, int32_t steps, int32_t *tile_x, int32_t *seg_y,
                        double *ms_per_step);
 

@@ -19,6 +19,7 @@ cudaError_t configure_fused_smem();
 namespace {
 
 constexpr int GRAPH_STEPS = 32;  // steps per captured graph (even: parity preserved)
+constexpr int BATCH_SIDE_STREAMS = 16;  // concurrent run chains in a batch's graph
 
 }  // namespace
 
@@ -746,7 +747,12 @@ int lbm_load_state(lbm_ctx* ctx, const char* path) {
 }  // extern "C"
 
 // ---------------------------------------------------------------------------
-// Batches: many runs advanced by one persistent launch per step
+// Batches: many runs advanced together.  Captured graphs of GRAPH_STEPS steps
+// hold one chain of single-run launches per run, spread over side streams
+// (the chains are independent, so the graph runs them concurrently and each
+// launch keeps its run's parameters in the constant bank); steps outside a
+// graph (and the failure-path test hook) use one persistent launch over the
+// tiles of all runs.  Both kernels run the same per-cell arithmetic.
 // ---------------------------------------------------------------------------
 
 struct lbm_batch {
@@ -767,6 +773,11 @@ struct lbm_batch {
     bool desc_valid = false;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     int pending_error = LBM_OK;
+    // graph capture: side streams for the per-run chains, fork/join events
+    int nside = 0;
+    cudaStream_t side[BATCH_SIDE_STREAMS] = {};
+    cudaEvent_t fork_ev = nullptr;
+    cudaEvent_t join_ev[BATCH_SIDE_STREAMS] = {};
 };
 
 namespace {
@@ -870,6 +881,7 @@ int batch_sync_desc(lbm_batch* b) {
                 std::memcmp(&b->hdesc[r].p, &c->kp, sizeof(lbm::KParams)) != 0;
     }
     if (!dirty) return LBM_OK;
+    batch_drop_graphs(b);  // the graphs' launches carry the old parities and parameters
     for (int r = 0; r < b->nruns; ++r) {
         b->hdesc[r].flip = b->runs[r]->cur ^ b->parity;
         b->hdesc[r].p = b->runs[r]->kp;
@@ -886,17 +898,53 @@ void batch_launch(lbm_batch* b, int parity, cudaStream_t st) {
                                parity, b->derr, st);
 }
 
+// One graph of GRAPH_STEPS steps: run r's chain of launches starts from
+// buffer parity ^ flip[r].  Runs go to the side streams largest first, each
+// to the stream with the fewest cells so far, so the chains end together.
 int batch_build_graph(lbm_batch* b, int parity) {
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return batch_fail(b, e);
-    int par = parity;
-    for (int s = 0; s < GRAPH_STEPS; ++s) {
-        batch_launch(b, par, b->cap_stream);
-        par ^= 1;
+    e = cudaEventRecord(b->fork_ev, b->cap_stream);
+    for (int k = 0; k < b->nside && e == cudaSuccess; ++k)
+        e = cudaStreamWaitEvent(b->side[k], b->fork_ev, 0);
+    int64_t load[BATCH_SIDE_STREAMS] = {};
+    bool* done = (bool*)std::calloc((size_t)b->nruns, sizeof(bool));
+    if (!done && e == cudaSuccess) e = cudaErrorMemoryAllocation;
+    for (int a = 0; a < b->nruns && e == cudaSuccess; ++a) {
+        int r = -1;
+        int64_t best = -1;
+        for (int q = 0; q < b->nruns; ++q) {
+            const int64_t cells = (int64_t)b->hdesc[q].p.nx * b->hdesc[q].p.ny;
+            if (!done[q] && cells > best) {
+                best = cells;
+                r = q;
+            }
+        }
+        done[r] = true;
+        int k = 0;
+        for (int q = 1; q < b->nside; ++q)
+            if (load[q] < load[k]) k = q;
+        load[k] += best;
+        const lbm::RunDesc& d = b->hdesc[r];
+        int src = parity ^ d.flip;
+        for (int s = 0; s < GRAPH_STEPS; ++s) {
+            lbm::launch_step_tma(d.p, b->runs[r]->ds, src, b->shape, d.tmap, b->derr, b->side[k]);
+            src ^= 1;
+        }
+        e = cudaGetLastError();
     }
-    e = cudaStreamEndCapture(b->cap_stream, &g);
-    if (e != cudaSuccess) return batch_fail(b, e);
+    std::free(done);
+    for (int k = 0; k < b->nside && e == cudaSuccess; ++k) {
+        e = cudaEventRecord(b->join_ev[k], b->side[k]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->cap_stream, b->join_ev[k], 0);
+    }
+    const cudaError_t ee = cudaStreamEndCapture(b->cap_stream, &g);
+    if (e == cudaSuccess) e = ee;
+    if (e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return batch_fail(b, e);
+    }
     e = cudaGraphInstantiate(&b->graph[parity], g, 0);
     cudaGraphDestroy(g);
     return batch_fail(b, e);
@@ -937,9 +985,18 @@ int lbm_batch_create(const lbm_params* params, int32_t nruns, void* stream, lbm_
         lbm_batch_destroy(b);
         return LBM_ERR_NOMEM;
     }
-    if (cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    if (cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming) != cudaSuccess) {
         lbm_batch_destroy(b);
         return LBM_ERR_CUDA;
+    }
+    for (int k = 0; k < std::min<int>(nruns, BATCH_SIDE_STREAMS); ++k) {
+        if (cudaStreamCreateWithFlags(&b->side[k], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&b->join_ev[k], cudaEventDisableTiming) != cudaSuccess) {
+            lbm_batch_destroy(b);
+            return LBM_ERR_CUDA;
+        }
+        b->nside = k + 1;
     }
     for (int r = 0; r < nruns; ++r) {
         lbm_params pr = params[r];
@@ -978,6 +1035,11 @@ void lbm_batch_destroy(lbm_batch* b) {
     cudaFree(b->ditems);
     cudaFree(b->derr);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    for (int k = 0; k < BATCH_SIDE_STREAMS; ++k) {
+        if (b->side[k]) cudaStreamDestroy(b->side[k]);
+        if (b->join_ev[k]) cudaEventDestroy(b->join_ev[k]);
+    }
+    if (b->fork_ev) cudaEventDestroy(b->fork_ev);
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
     delete b;
 }
@@ -1180,6 +1242,7 @@ int lbm_autotune(lbm_ctx* ctx, int32_t steps, int32_t* tile_x, int32_t* seg_y,
 int lbm_batch_autotune(lbm_batch* b, int32_t steps, int32_t* tile_x, int32_t* seg_y,
                        double* ms_per_step) {
     if (!b || steps < 1) return LBM_ERR_INVALID_ARG;
+    const int tsteps = (steps + GRAPH_STEPS - 1) / GRAPH_STEPS * GRAPH_STEPS;
     int rc = lbm_batch_synchronize(b);
     if (rc != LBM_OK) return rc;
     float** snap = (float**)std::calloc((size_t)b->nruns, sizeof(float*));
@@ -1216,15 +1279,16 @@ int lbm_batch_autotune(lbm_batch* b, int32_t steps, int32_t* tile_x, int32_t* se
         for (int k = 0; k < 7 && rc == LBM_OK; ++k) {
             rc = lbm_batch_set_launch_shape(b, bxs[a], segs[k]);
             if (rc != LBM_OK) break;
-            rc = lbm_batch_step(b, 2);
+            // whole graphs, as long runs step: the first one builds the graph
+            rc = lbm_batch_step(b, GRAPH_STEPS);
             if (rc == LBM_OK) rc = batch_fail(b, cudaEventRecord(e0, b->stream));
-            if (rc == LBM_OK) rc = lbm_batch_step(b, steps);
+            if (rc == LBM_OK) rc = lbm_batch_step(b, tsteps);
             if (rc == LBM_OK) rc = batch_fail(b, cudaEventRecord(e1, b->stream));
             if (rc == LBM_OK) rc = lbm_batch_synchronize(b);
             float ms = 0.0f;
             if (rc == LBM_OK) rc = batch_fail(b, cudaEventElapsedTime(&ms, e0, e1));
-            if (rc == LBM_OK && ms / steps < best) {
-                best = ms / steps;
+            if (rc == LBM_OK && ms / tsteps < best) {
+                best = ms / tsteps;
                 best_shape = lbm::FusedShape{bxs[a], segs[k]};
             }
             for (int r = 0; r < b->nruns && ce == cudaSuccess; ++r) {

@@ -97,8 +97,10 @@ struct CellOut {
 
 // Flow part of one cell's collisions (App. D): forces, velocity, pressure
 // and, with do_collide, the flow populations gg collided in place.
+// out_scale: power-of-two factor on the output populations (16-bit storage).
 __device__ __forceinline__ CellOut collide_flow_cell(const KParams& p, const CellGeom& g, int j,
-                                                     float gg[9], bool do_collide) {
+                                                     float gg[9], bool do_collide,
+                                                     float out_scale = 1.0f) {
     CellOut o;
     // surface-tension force, Eq. (Fs)
     const float g2 = g.gm * g.gm;
@@ -136,8 +138,8 @@ __device__ __forceinline__ CellOut collide_flow_cell(const KParams& p, const Cel
         m.Fpx = Fpx;
         m.Fpy = Fpy;
         m.w_nu = p.nu_uniform ? p.w_nu : rate_from_coeff(lerp_phase(p, g.phi, p.nu_a, p.nu_b));
-        collide_flow(gg, m, p.w_zeta);
-        wall_correct_flow(gg, p, j, rho);
+        collide_flow(gg, m, p.w_zeta, out_scale);
+        wall_correct_flow(gg, p, j, rho, out_scale);
     }
     return o;
 }
@@ -148,14 +150,15 @@ __device__ __forceinline__ CellOut collide_flow_cell(const KParams& p, const Cel
 __device__ __forceinline__ void collide_scalars_cell(const KParams& p, int phi_fx, float phi,
                                                      float c, float nx, float ny, float ux,
                                                      float uy, float fjx, float fjy, float hjx,
-                                                     float hjy, float df[9], float dh[9]) {
+                                                     float hjy, float df[9], float dh[9],
+                                                     float sf = 1.0f, float sh = 1.0f) {
     // Eq. (theta) and the theta_c of Eq. (ISS)
     float theta, theta_c;
     interface_coeffs(p, phi_fx, c, theta, theta_c);
     collide_scalar_dev(phi, fjx, fjy, p.M_phi * theta * nx, p.M_phi * theta * ny, p.w_kappa, ux,
-                       uy, df);
+                       uy, df, sf);
     collide_scalar_dev(c, hjx, hjy, p.D_s * theta_c * nx, p.D_s * theta_c * ny, p.w_chi, ux, uy,
-                       dh);
+                       dh, sh);
 }
 
 // The three collisions of one cell at row j.  f and h enter as their first

@@ -165,11 +165,14 @@ constexpr int FX_INVALID = INT_MIN;
 constexpr int FX_RANGE = 1 << 30;  // |value| beyond this (twice the bounds) is invalid
 
 // Fixed-point value after adding a float increment.
+// An invalid s0 needs no test of its own: INT_MIN plus an increment below
+// 1e9 < 2^30 in magnitude lands outside [-FX_RANGE, FX_RANGE] (the sum is
+// formed in unsigned arithmetic, so it wraps instead of overflowing).
 __device__ __forceinline__ int fx_add(int s0, float inc, float scale) {
     const float v = inc * scale;
-    if (s0 == FX_INVALID || !(fabsf(v) < 1.0e9f)) return FX_INVALID;
-    const int r = s0 + __float2int_rn(v);
-    return (r > FX_RANGE || r < -FX_RANGE) ? FX_INVALID : r;
+    if (!(fabsf(v) < 1.0e9f)) return FX_INVALID;
+    const unsigned r = (unsigned)s0 + (unsigned)__float2int_rn(v);
+    return r + (unsigned)FX_RANGE > 2u * (unsigned)FX_RANGE ? FX_INVALID : (int)r;
 }
 
 // Float value of a fixed-point number (NaN for the invalid marker).
@@ -341,20 +344,23 @@ __device__ __forceinline__ float sigma_of_c(const KParams& p, float c) {
 // collisions
 // ---------------------------------------------------------------------------
 
-// P^-1 applied to raw moments r = (00,10,01,20,02,11,21,12,22) (App. A).
-__device__ __forceinline__ void raw_to_pops(const float r[9], float out[9]) {
+// P^-1 applied to raw moments r = (00,10,01,20,02,11,21,12,22) (App. A),
+// times s (a power of two: the 16-bit storage scale, folded into the factors
+// 1/2 and 1/4 at no cost and without rounding; 1 for FP32 storage).
+__device__ __forceinline__ void raw_to_pops(const float r[9], float out[9], float s = 1.0f) {
     // factored: the eight pair sums and differences are shared by two outputs each
     const float a = r[3] - r[8], b = r[1] - r[7], c = r[4] - r[8], d = r[2] - r[6];
     const float e = r[8] + r[5], f = r[6] + r[7], g = r[8] - r[5], h = r[6] - r[7];
-    out[0] = (r[0] - r[3]) - c;
-    out[1] = 0.5f * (a + b);
-    out[2] = 0.5f * (c + d);
-    out[3] = 0.5f * (a - b);
-    out[4] = 0.5f * (c - d);
-    out[5] = 0.25f * (e + f);
-    out[6] = 0.25f * (g + h);
-    out[7] = 0.25f * (e - f);
-    out[8] = 0.25f * (g - h);
+    const float h2 = 0.5f * s, h4 = 0.25f * s;
+    out[0] = ((r[0] - r[3]) - c) * s;
+    out[1] = h2 * (a + b);
+    out[2] = h2 * (c + d);
+    out[3] = h2 * (a - b);
+    out[4] = h2 * (c - d);
+    out[5] = h4 * (e + f);
+    out[6] = h4 * (g + h);
+    out[7] = h4 * (e - f);
+    out[8] = h4 * (g - h);
 }
 
 // F^-1(u) applied to central moments k (binomial expansion of ((e-u)+u)^m).
@@ -401,7 +407,8 @@ __device__ __forceinline__ void collide_scalar(float a[9], float s, float qx, fl
 // s (raw moments of the equilibrium shape at u minus those at rest) plus the
 // raw moments of F^-1(u) (0, k10~, k01~, 0, ...), so no O(s) term is formed.
 __device__ __forceinline__ void collide_scalar_dev(float s, float jx, float jy, float qx, float qy,
-                                                   float w, float ux, float uy, float d[9]) {
+                                                   float w, float ux, float uy, float d[9],
+                                                   float out_scale = 1.0f) {
     const float k10 = jx - ux * s, k01 = jy - uy * s;
     const float a = k10 + w * (qx - k10);
     const float b = k01 + w * (qy - k01);
@@ -416,7 +423,7 @@ __device__ __forceinline__ void collide_scalar_dev(float s, float jx, float jy, 
     R[6] = s * (ux2 * uy + uy * CS2) + 2.0f * uxy * a + ux2 * b;
     R[7] = s * (ux * uy2 + ux * CS2) + uy2 * a + 2.0f * uxy * b;
     R[8] = s * (ux2 * uy2 + CS2 * (ux2 + uy2)) + 2.0f * ux * uy2 * a + 2.0f * ux2 * uy * b;
-    raw_to_pops(R, d);
+    raw_to_pops(R, d, out_scale);
 }
 
 // Macroscopic inputs of the flow collision at one cell.
@@ -434,7 +441,10 @@ struct FlowMacro {
 // a = g - w P0.  Central moments of the shift are P0 W(u) with W(u) the
 // central moments of the weights about u; they cancel in eq - moments, so the
 // collision runs on deviations: d_eta^eq = rho cs2 (M(u) - W(u)) + dP W(u).
-__device__ __forceinline__ void collide_flow(float a[9], const FlowMacro& m, float w_zeta) {
+// out_scale: power-of-two factor applied to the output populations (16-bit
+// storage scale; 1 for FP32 storage).
+__device__ __forceinline__ void collide_flow(float a[9], const FlowMacro& m, float w_zeta,
+                                             float out_scale = 1.0f) {
     const float ux = m.ux, uy = m.uy;
     const float ux2 = ux * ux, uy2 = uy * uy, uxy = ux * uy;
     // raw moments of the shifted populations that relax at non-unit rates
@@ -488,23 +498,24 @@ __device__ __forceinline__ void collide_flow(float a[9], const FlowMacro& m, flo
     // Explicit FMAs: every kernel that inlines this rounds it the same way.
     r[1] = __fmaf_rn(CS2, m.Ftx, jx);
     r[2] = __fmaf_rn(CS2, m.Fty, jy);
-    raw_to_pops(r, a);
+    raw_to_pops(r, a, out_scale);
 }
 
 // Moving-wall term added when a flow population is written into a slot that
 // is only read back by the bounce-back of the same cell (App. D set-up,
 // half-way bounce-back): slot q at the bottom row (e_qy = -1) feeds direction
 // opp(q) with u_w = (-u_wall, 0); at the top row (e_qy = +1) u_w = (+u_wall, 0).
-__device__ __forceinline__ void wall_correct_flow(float a[9], const KParams& p, int j, float rho) {
+__device__ __forceinline__ void wall_correct_flow(float a[9], const KParams& p, int j, float rho,
+                                                  float out_scale = 1.0f) {
     if (!p.walls) return;
     if (j == 0) {
         // 2 w_opp rho (e_opp . u_w), u_w = -u_wall: opp(4)=2 (0), opp(7)=5 (+1), opp(8)=6 (-1)
-        const float t = 2.0f * (1.0f / 36.0f) * rho * (-p.u_wall);
+        const float t = 2.0f * (1.0f / 36.0f) * rho * (-p.u_wall) * out_scale;
         a[7] += t;   // e_5x = +1
         a[8] -= t;   // e_6x = -1
     }
     if (j == p.ny - 1) {
-        const float t = 2.0f * (1.0f / 36.0f) * rho * (p.u_wall);
+        const float t = 2.0f * (1.0f / 36.0f) * rho * (p.u_wall) * out_scale;
         a[5] -= t;   // opp(5) = 7, e_7x = -1
         a[6] += t;   // opp(6) = 8, e_8x = +1
     }

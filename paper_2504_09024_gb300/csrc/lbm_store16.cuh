@@ -83,24 +83,18 @@ __device__ __forceinline__ uint32_t word_bits(uint32_t h, int k) {
     return h * (0x9E3779B1u + 2u * (uint32_t)k * 0x632BE5ABu);
 }
 
-// (a, b) rounded to the 16-bit format with random bits r (16 per value):
-// add uniform bits below the kept precision to the magnitude, then truncate.
-// FP16: 13 dropped mantissa bits for values in the normal range (smaller
-// values keep a truncation bias below 2^-24 of the scaled value).
+// (a, b) rounded stochastically to the 16-bit format, a in the low half:
+// the sm_100-family conversion cvt.rs rounds away from zero with probability
+// equal to the dropped fraction, drawing 16 random bits per value (the upper
+// half of r for its first operand, which lands in the upper half of the word).
 template <int ST>
 __device__ __forceinline__ uint32_t pack2_sr(float a, float b, uint32_t r) {
-    if constexpr (ST == ST_BF16) {
-        const uint32_t ua = __float_as_uint(a) + (r & 0xFFFFu);
-        const uint32_t ub = __float_as_uint(b) + (r >> 16);
-        return (ua >> 16) | (ub & 0xFFFF0000u);
-    } else {
-        const float ra = __uint_as_float(__float_as_uint(a) + (r & 0x1FFFu));
-        const float rb = __uint_as_float(__float_as_uint(b) + ((r >> 16) & 0x1FFFu));
-        const __half2 h = __halves2half2(__float2half_rz(ra), __float2half_rz(rb));
-        uint32_t w;
-        memcpy(&w, &h, 4);
-        return w;
-    }
+    uint32_t w;
+    if constexpr (ST == ST_BF16)
+        asm("cvt.rs.bf16x2.f32 %0, %1, %2, %3;" : "=r"(w) : "f"(b), "f"(a), "r"(r));
+    else
+        asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;" : "=r"(w) : "f"(b), "f"(a), "r"(r));
+    return w;
 }
 
 __device__ __forceinline__ uint32_t word_at(const float* p) { return __float_as_uint(*p); }
@@ -116,21 +110,23 @@ __device__ __forceinline__ void pull_pair16(const float* __restrict__ Rm,
                                             ScalarMoments& mf, ScalarMoments& mh) {
     const int Sf0 = __float_as_int(R0[c0]);
     const int Sh0 = __float_as_int(R0[P16_SH * PS + c0]);
-    const float qf = p.qinv[0], qh = p.qinv[1];
+    // The sums run on the scaled deviations and are unscaled once at the end
+    // (the weights carry the scale instead): the scales are powers of two, so
+    // moving them costs no accuracy, and it saves a multiply per value.
     float of[9], oh[9];
 #pragma unroll
     for (int q = 1; q < 9; ++q) {
         const float2 v = unpack2<ST>(word_at(R0 + (P16_FH - 1 + q) * PS + c0));
-        of[q] = v.x * qf;
-        oh[q] = v.y * qh;
+        of[q] = v.x;
+        oh[q] = v.y;
     }
-    const float wf1 = (1.0f / 9.0f) * p.fx_inv[0], wf5 = (1.0f / 36.0f) * p.fx_inv[0];
-    const float wh1 = (1.0f / 9.0f) * p.fx_inv[1], wh5 = (1.0f / 36.0f) * p.fx_inv[1];
+    const float wf1 = ((1.0f / 9.0f) * p.fx_inv[0]) * p.qs[0], wf5 = ((1.0f / 36.0f) * p.fx_inv[0]) * p.qs[0];
+    const float wh1 = ((1.0f / 9.0f) * p.fx_inv[1]) * p.qs[1], wh5 = ((1.0f / 36.0f) * p.fx_inv[1]) * p.qs[1];
     float tf[9], th[9];
     auto pulled = [&](int q, const float* R, int col, bool diag) {
         const float2 v = unpack2<ST>(word_at(R + (P16_FH - 1 + q) * PS + col));
-        tf[q] = (diag ? wf5 : wf1) * (float)(__float_as_int(R[col]) - Sf0) + v.x * qf;
-        th[q] = (diag ? wh5 : wh1) * (float)(__float_as_int(R[P16_SH * PS + col]) - Sh0) + v.y * qh;
+        tf[q] = (diag ? wf5 : wf1) * (float)(__float_as_int(R[col]) - Sf0) + v.x;
+        th[q] = (diag ? wh5 : wh1) * (float)(__float_as_int(R[P16_SH * PS + col]) - Sh0) + v.y;
     };
     pulled(1, R0, cm, false);
     pulled(3, R0, cp, false);
@@ -152,15 +148,15 @@ __device__ __forceinline__ void pull_pair16(const float* __restrict__ Rm,
         pulled(7, Rp, cp, true);
         pulled(8, Rp, cm, true);
     }
-    auto moments = [](int S0, const float t[9], const float o[9], ScalarMoments& m) {
+    auto moments = [](int S0, const float t[9], const float o[9], float qi, ScalarMoments& m) {
         m.s0 = S0;
-        m.inc = (((t[1] + t[3]) + (t[2] + t[4])) + ((t[5] + t[6]) + (t[7] + t[8]))) -
-                (((o[1] + o[3]) + (o[2] + o[4])) + ((o[5] + o[6]) + (o[7] + o[8])));
-        m.jx = (t[1] - t[3]) + (t[5] - t[6]) - (t[7] - t[8]);
-        m.jy = (t[2] - t[4]) + (t[5] + t[6]) - (t[7] + t[8]);
+        m.inc = ((((t[1] + t[3]) + (t[2] + t[4])) + ((t[5] + t[6]) + (t[7] + t[8]))) -
+                 (((o[1] + o[3]) + (o[2] + o[4])) + ((o[5] + o[6]) + (o[7] + o[8])))) * qi;
+        m.jx = ((t[1] - t[3]) + (t[5] - t[6]) - (t[7] - t[8])) * qi;
+        m.jy = ((t[2] - t[4]) + (t[5] + t[6]) - (t[7] + t[8])) * qi;
     };
-    moments(Sf0, tf, of, mf);
-    moments(Sh0, th, oh, mh);
+    moments(Sf0, tf, of, p.qinv[0], mf);
+    moments(Sh0, th, oh, p.qinv[1], mh);
 }
 
 // Post-streaming flow populations (shifted, unscaled) from staged 16-bit rows.

@@ -357,19 +357,20 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap* tmap, const KParam
                     float gg[9];
 #pragma unroll
                     for (int q = 0; q < 9; ++q) gg[q] = kg[2][q];
-                    const CellOut o = collide_flow_cell(p, g, jc, gg, true);
+                    // 16-bit storage: the collision leaves the populations scaled for packing
+                    const CellOut o =
+                        collide_flow_cell(p, g, jc, gg, true, ST == ST_F32 ? 1.0f : p.qs[2]);
                     s_ux[(jc & 1) * BX + t] = o.ux;
                     s_uy[(jc & 1) * BX + t] = o.uy;
                     const int64_t idx = (int64_t)jc * p.pitch + i;
                     if constexpr (ST == ST_F32) {
                         store9(dst + 18 * p.plane, p, idx, i, gg);
                     } else {
-                        const float sg = p.qs[2];
                         const uint32_t seed = pcg_hash(step_seed ^ (uint32_t)(jc * p.nx + i) ^ 0x80000000u);
                         uint32_t w[5];
 #pragma unroll
                         for (int k = 0; k < 5; ++k)
-                            w[k] = pack2_sr<ST>(gg[2 * k] * sg, 2 * k + 1 < 9 ? gg[2 * k + 1] * sg : 0.0f,
+                            w[k] = pack2_sr<ST>(gg[2 * k], 2 * k + 1 < 9 ? gg[2 * k + 1] : 0.0f,
                                                 word_bits(seed, 9 + k));
                         const int gs[2] = {ghost_right(p, i), ghost_left(p, i)};
                         store_words<5>(dst, p.plane, idx, gs, P16_G, w);
@@ -392,25 +393,25 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap* tmap, const KParam
                         ux = s_ux[(jc & 1) * BX + t];
                         uy = s_uy[(jc & 1) * BX + t];
                     } else {
-                        const int64_t fi = idx;
-                        ux = F[FP_UX * p.plane + fi];
-                        uy = F[FP_UY * p.plane + fi];
+                        ux = F[FP_UX * p.plane + idx];
+                        uy = F[FP_UY * p.plane + idx];
                     }
                     float df[9], dh[9];
                     collide_scalars_cell(p, phi_fx, (float)phi_fx * p.fx_inv[0], s_c[c0 * BX + t],
                                          s_nx[n0 * BX + t], s_ny[n0 * BX + t], ux, uy, ks[3][0],
-                                         ks[3][1], ks[3][3], ks[3][4], df, dh);
+                                         ks[3][1], ks[3][3], ks[3][4], df, dh,
+                                         ST == ST_F32 ? 1.0f : p.qs[0],
+                                         ST == ST_F32 ? 1.0f : p.qs[1]);
                     if constexpr (ST == ST_F32) {
                         store_dev(dst, p, idx, i, phi_fx, df);
                         store_dev(dst + 9 * p.plane, p, idx, i, __float_as_int(ks[3][2]), dh);
                     } else {
-                        const float sf = p.qs[0], sh = p.qs[1];
                         const uint32_t seed = pcg_hash(step_seed ^ (uint32_t)(jc * p.nx + i));
                         uint32_t w[10];
                         w[0] = (uint32_t)phi_fx;
                         w[1] = __float_as_uint(ks[3][2]);
 #pragma unroll
-                        for (int q = 1; q < 9; ++q) w[1 + q] = pack2_sr<ST>(df[q] * sf, dh[q] * sh, word_bits(seed, q));
+                        for (int q = 1; q < 9; ++q) w[1 + q] = pack2_sr<ST>(df[q], dh[q], word_bits(seed, q));
                         const int gs[2] = {ghost_right(p, i), ghost_left(p, i)};
                         store_words<10>(dst, p.plane, idx, gs, 0, w);
                     }
