@@ -378,6 +378,27 @@ __device__ __forceinline__ void central_to_raw(const float k[9], float ux, float
            ux2 * k[4] + 4.0f * uxy * k[5] + 2.0f * uy * k[6] + 2.0f * ux * k[7] + k[8];
 }
 
+// The same transform as central_to_raw, applied as two one-dimensional shifts
+// (F^-1(u) is the tensor product of the x and y binomial shifts): per order-2
+// triple (c0, c1, c2) -> (c0, c1 + u c0, c2 + u (c1 + (c1 + u c0))).
+__device__ __forceinline__ void central_to_raw_sep(const float k[9], float ux, float uy,
+                                                   float r[9]) {
+    // x shift of the rows b = 0, 1, 2 (k indices: 00 0, 10 1, 20 3 | 01 2, 11 5, 21 6 | 02 4, 12 7, 22 8)
+    const float m10 = k[1] + ux * k[0], m20 = k[3] + ux * (k[1] + m10);
+    const float m11 = k[5] + ux * k[2], m21 = k[6] + ux * (k[5] + m11);
+    const float m12 = k[7] + ux * k[4], m22 = k[8] + ux * (k[7] + m12);
+    // y shift of the columns a = 0, 1, 2
+    r[0] = k[0];
+    r[2] = k[2] + uy * k[0];
+    r[4] = k[4] + uy * (k[2] + r[2]);
+    r[1] = m10;
+    r[5] = m11 + uy * m10;
+    r[7] = m12 + uy * (m11 + r[5]);
+    r[3] = m20;
+    r[6] = m21 + uy * m20;
+    r[8] = m22 + uy * (m21 + r[6]);
+}
+
 // Advection-diffusion lattice (f with s = phi, q = M_phi theta n; or h with
 // s = c, q = D_s theta_c n): all central moments are set to their equilibria
 // (s, q, cs2 s, cs2 s, 0, 0, 0, cs4 s) except the first-order ones, which
@@ -488,7 +509,7 @@ __device__ __forceinline__ void collide_flow(float a[9], const FlowMacro& m, flo
     k[7] = RmP * (uy2 + CS2) * ux;
     k[8] = -R * (ux2 * uy2 + CS2 * (ux2 + uy2)) + dP * (ux2 + CS2) * (uy2 + CS2);
     float r[9];
-    central_to_raw(k, ux, uy, r);
+    central_to_raw_sep(k, ux, uy, r);
     // The raw first moments of the post-collision state are exactly
     // rho cs2 u + cs2 F_t / 2 = j + cs2 F_t (j: pre-collision momentum, with
     // rho cs2 u = j + cs2 F_t / 2).  Formed from j they carry the momentum

@@ -272,37 +272,30 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap* tmap, const KParam
                 named_bar_or(false, NT);
             }
             // ---------------- B: unit normal one row behind ----------------
-            if (FLOW && sweep) {
-                for (int pass = 0; pass < 2; ++pass) {
-                    int rn = r - 1;
-                    if (pass == 1) {
-                        // with a bottom wall, n(-1) needs the mirror of row 1, available at r = 1
-                        if (!(p.walls && r == 1 && y0 == 0)) break;
-                        rn = -1;
-                    } else if (p.walls && rn == -1) {
-                        continue;
-                    }
-                    if (role >= 2 && rn >= y0 - 1 && rn <= y1) {
-                        // pass 0: rows r-2, r-1, r
-                        const int sm1 = pass ? rmod(rn - 1, T_RING) : wrap_once<T_RING>(s5 + 3);
-                        const int s0 = pass ? rmod(rn, T_RING) : wrap_once<T_RING>(s5 + 4);
-                        const int sp1 = pass ? rmod(rn + 1, T_RING) : s5;
-                        int v[3][3];
+            if (FLOW && sweep && role >= 2) {
+                // normal of row rn from the phi ring slots of rows rn-1, rn, rn+1
+                auto normal_row = [&](int sm1, int s0, int sp1, int ns) {
+                    int v[3][3];
 #pragma unroll
-                        for (int e = 0; e < 3; ++e) {
-                            v[0][e] = s_phi[sm1 * BX + t - 1 + e];
-                            v[1][e] = s_phi[s0 * BX + t - 1 + e];
-                            v[2][e] = s_phi[sp1 * BX + t - 1 + e];
-                        }
-                        float gx, gy, nx, ny, gm;
-                        iso_grad_fx(v, p.fx_inv[0], gx, gy);
-                        unit_normal(gx, gy, nx, ny, gm);
-                        const int ns = pass ? rmod(rn, T_NRING) : wrap_once<T_NRING>(s3 + 2);
-                        s_nx[ns * BX + t] = nx;
-                        s_ny[ns * BX + t] = ny;
-                        s_gm[ns * BX + t] = gm;
+                    for (int e = 0; e < 3; ++e) {
+                        v[0][e] = s_phi[sm1 * BX + t - 1 + e];
+                        v[1][e] = s_phi[s0 * BX + t - 1 + e];
+                        v[2][e] = s_phi[sp1 * BX + t - 1 + e];
                     }
-                }
+                    float gx, gy, nx, ny, gm;
+                    iso_grad_fx(v, p.fx_inv[0], gx, gy);
+                    unit_normal(gx, gy, nx, ny, gm);
+                    s_nx[ns * BX + t] = nx;
+                    s_ny[ns * BX + t] = ny;
+                    s_gm[ns * BX + t] = gm;
+                };
+                const int rn = r - 1;  // rows r-2, r-1, r
+                if (rn >= y0 - 1 && rn <= y1 && !(p.walls && rn == -1))
+                    normal_row(wrap_once<T_RING>(s5 + 3), wrap_once<T_RING>(s5 + 4), s5,
+                               wrap_once<T_NRING>(s3 + 2));
+                // with a bottom wall, n(-1) needs the mirror of row 1, available at r = 1
+                if (p.walls && r == 1 && y0 == 0)
+                    normal_row(rmod(-2, T_RING), rmod(-1, T_RING), rmod(0, T_RING), rmod(-1, T_NRING));
             }
             // the flow group's own barrier: its collisions read the normals
             // its other warps just formed (group 0 does not wait here)
