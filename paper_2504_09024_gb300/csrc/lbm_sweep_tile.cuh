@@ -190,7 +190,6 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap* tmap, const KParam
                     const float* Rm = staged(r - 1);
                     const float* R0 = staged(r);
                     const float* Rp = staged(r + 1);
-                    const bool keep = role == 3 && r >= y0 && r < y1;
                     if constexpr (!FLOW) {
                         ScalarMoments m, mh;
                         if constexpr (ST == ST_F32) {
@@ -224,10 +223,11 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap* tmap, const KParam
                         else
                             pull9_16<ST>(Rm, R0, Rp, W, cs - 1, cs, cs + 1, bot, top, p.qinv[2], a);
                         s_dps[slot * BX + t] = sum9(a);
-                        if (keep) {
+                        // every pulled row enters the ring: rows and columns that do not
+                        // collide never read it, and an unconditional write lets the pull
+                        // land in the ring's registers directly
 #pragma unroll
-                            for (int q = 0; q < 9; ++q) kg[0][q] = a[q];
-                        }
+                        for (int q = 0; q < 9; ++q) kg[0][q] = a[q];
                     }
                     // mirror rows below the bottom wall, formed once rows 0 and 1 exist
                     if (p.walls && r == 1) {
