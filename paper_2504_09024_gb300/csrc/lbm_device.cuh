@@ -322,17 +322,12 @@ __device__ __forceinline__ float iso_div(const float vx[3][3], const float vy[3]
 }
 
 __device__ __forceinline__ void unit_normal(float gx, float gy, float& nx, float& ny, float& mag) {
+    // branch-free: below the threshold the normal and the magnitude are 0
     const float g2 = gx * gx + gy * gy;
-    if (g2 > EPS_N * EPS_N) {
-        const float inv = rsqrtf(g2);  // within 2 ulp; n and |grad phi| to ~1e-7
-        nx = gx * inv;
-        ny = gy * inv;
-        mag = g2 * inv;
-    } else {
-        nx = 0.0f;
-        ny = 0.0f;
-        mag = sqrtf(g2);
-    }
+    const float inv = g2 > EPS_N * EPS_N ? rsqrtf(g2) : 0.0f;  // rsqrt within 2 ulp
+    nx = gx * inv;
+    ny = gy * inv;
+    mag = g2 * inv;
 }
 
 // Langmuir isotherm, Eq. (EOS).

@@ -184,7 +184,11 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap* tmap, const KParam
                 bool ok = true;
                 if (r == rs) ok = wait_row(r - 1) && wait_row(r);
                 ok = ok && wait_row(r + 1);
-                if (ok && role > 0) {
+                // Every thread forms the moments of its column, including the halo
+                // columns whose results nobody reads and, in a ragged last tile,
+                // columns beyond the grid (their staged values are padding or
+                // fill): per-thread tests here cost more than the idle lanes save.
+                if (ok) {
                     const int jj = p.walls ? r : wrap_i(r, p.ny);
                     const bool bot = p.walls && jj == 0, top = p.walls && jj == p.ny - 1;
                     const float* Rm = staged(r - 1);
@@ -201,7 +205,7 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap* tmap, const KParam
                         s_phi[slot * BX + t] = fx_add(m.s0, m.inc, p.fx_scale[0]);
                         ks[0][0] = m.jx;
                         ks[0][1] = m.jy;
-                        if (role >= 2) {
+                        {  // h: c and sigma(c)
                             if constexpr (ST == ST_F32)
                                 m = pull_scalar_rows(Rm + 9 * W, R0 + 9 * W, Rp + 9 * W, W, cs - 1,
                                                      cs, cs + 1, bot, top, p.fx_inv[1]);
@@ -215,7 +219,7 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap* tmap, const KParam
                             ks[0][3] = m.jx;
                             ks[0][4] = m.jy;
                         }
-                    } else if (COUPLED && role >= 2) {
+                    } else if (COUPLED) {
                         float a[9];
                         if constexpr (ST == ST_F32)
                             pull9_rows(Rm + 18 * W, R0 + 18 * W, Rp + 18 * W, W, cs - 1, cs, cs + 1,
@@ -272,7 +276,7 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap* tmap, const KParam
                 named_bar_or(false, NT);
             }
             // ---------------- B: unit normal one row behind ----------------
-            if (FLOW && sweep && role >= 2) {
+            if (FLOW && sweep && role > 0) {
                 // normal of row rn from the phi ring slots of rows rn-1, rn, rn+1
                 auto normal_row = [&](int sm1, int s0, int sp1, int ns) {
                     int v[3][3];
