@@ -117,6 +117,9 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap* tmap, const KParam
     else if (col == x0 - 1 || col == xend) role = 2;
     else if (col == x0 - 2 || col == xend + 1) role = 1;
     const int i = wrap_i(col, p.nx);
+    // ghost copies of column i, fixed per tile (FP32 stores; the 16-bit stores
+    // form them per call, which measured faster there)
+    const int gsT[2] = {ghost_right(p, i), ghost_left(p, i)};
     const int cs = t + 2;  // this column's index in a staged row (staged column 0 is x0 - 4)
 
     // rows swept: phi for y0-2 .. y1+1; beyond walls only mirror copies
@@ -361,7 +364,10 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap* tmap, const KParam
                     s_uy[(jc & 1) * BX + t] = o.uy;
                     const int64_t idx = (int64_t)jc * p.pitch + i;
                     if constexpr (ST == ST_F32) {
-                        store9(dst + 18 * p.plane, p, idx, i, gg);
+                        uint32_t w[9];
+#pragma unroll
+                        for (int q = 0; q < 9; ++q) w[q] = __float_as_uint(gg[q]);
+                        store_words<9>(dst, p.plane, idx, gsT, 18, w);
                     } else {
                         const uint32_t seed = pcg_hash(step_seed ^ (uint32_t)(jc * p.nx + i) ^ 0x80000000u);
                         uint32_t w[5];
@@ -400,8 +406,15 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap* tmap, const KParam
                                          ST == ST_F32 ? 1.0f : p.qs[0],
                                          ST == ST_F32 ? 1.0f : p.qs[1]);
                     if constexpr (ST == ST_F32) {
-                        store_dev(dst, p, idx, i, phi_fx, df);
-                        store_dev(dst + 9 * p.plane, p, idx, i, __float_as_int(ks[3][2]), dh);
+                        uint32_t w[9];
+                        w[0] = (uint32_t)phi_fx;
+#pragma unroll
+                        for (int q = 1; q < 9; ++q) w[q] = __float_as_uint(df[q]);
+                        store_words<9>(dst, p.plane, idx, gsT, 0, w);
+                        w[0] = __float_as_uint(ks[3][2]);
+#pragma unroll
+                        for (int q = 1; q < 9; ++q) w[q] = __float_as_uint(dh[q]);
+                        store_words<9>(dst, p.plane, idx, gsT, 9, w);
                     } else {
                         const uint32_t seed = pcg_hash(step_seed ^ (uint32_t)(jc * p.nx + i));
                         uint32_t w[10];
