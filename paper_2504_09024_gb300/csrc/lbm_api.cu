@@ -638,7 +638,8 @@ int lbm_set_launch_shape(lbm_ctx* ctx, int32_t tile_x, int32_t seg_y) {
         return LBM_ERR_INVALID_ARG;
     if (seg_y != 0 && seg_y < 4) return LBM_ERR_INVALID_ARG;
     const bool ok_bx = tile_x == 0 || tile_x == 128 ||
-                       (tile_x == 64 && ctx->kernel == LBM_KERNEL_TMA && ctx->st == lbm::ST_F32);
+                       ((tile_x == 64 || tile_x == 192) && ctx->kernel == LBM_KERNEL_TMA &&
+                        ctx->st == lbm::ST_F32);
     if (!ok_bx) return LBM_ERR_UNSUPPORTED;
     if (tile_x) ctx->shape.bx = tile_x;
     if (seg_y) ctx->shape.seg = seg_y;
@@ -1113,7 +1114,7 @@ int lbm_batch_synchronize(lbm_batch* b) {
 
 int lbm_batch_set_launch_shape(lbm_batch* b, int32_t tile_x, int32_t seg_y) {
     if (!b) return LBM_ERR_INVALID_ARG;
-    if (tile_x != 0 && tile_x != 64 && tile_x != 128) return LBM_ERR_UNSUPPORTED;
+    if (tile_x != 0 && tile_x != 64 && tile_x != 128 && tile_x != 192) return LBM_ERR_UNSUPPORTED;
     if (seg_y != 0 && seg_y < 4) return LBM_ERR_INVALID_ARG;
     const int rc = lbm_batch_synchronize(b);
     if (rc != LBM_OK) return rc;
@@ -1195,8 +1196,8 @@ int lbm_autotune(lbm_ctx* ctx, int32_t steps, int32_t* tile_x, int32_t* seg_y,
     if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
     double best = 1e300;
     lbm::FusedShape best_shape = shape0;
-    const int bxs[2] = {128, 64};
-    const int nbx = ctx->kernel == LBM_KERNEL_TMA && ctx->st == lbm::ST_F32 ? 2 : 1;
+    const int bxs[3] = {128, 192, 64};
+    const int nbx = ctx->kernel == LBM_KERNEL_TMA && ctx->st == lbm::ST_F32 ? 3 : 1;
     for (int a = 0; a < nbx && ce == cudaSuccess && rc == LBM_OK; ++a) {
         const int bx = bxs[a];
         const int per_sm = ctx->kernel != LBM_KERNEL_TMA ? 2
@@ -1273,9 +1274,9 @@ int lbm_batch_autotune(lbm_batch* b, int32_t steps, int32_t* tile_x, int32_t* se
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (ce == cudaSuccess) ce = cudaEventCreate(&e0);
     if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
-    const int bxs[2] = {128, 64};
+    const int bxs[3] = {128, 192, 64};
     const int segs[7] = {16, 24, 32, 48, 64, 96, 128};
-    for (int a = 0; a < 2 && ce == cudaSuccess && rc == LBM_OK; ++a) {
+    for (int a = 0; a < 3 && ce == cudaSuccess && rc == LBM_OK; ++a) {
         for (int k = 0; k < 7 && rc == LBM_OK; ++k) {
             rc = lbm_batch_set_launch_shape(b, bxs[a], segs[k]);
             if (rc != LBM_OK) break;

@@ -105,13 +105,17 @@ bool make_tensor_map(CUtensorMap* map, float* alloc, const KParams& p, int nplan
     return r == CUDA_SUCCESS;
 }
 
-size_t tma_smem_bytes(int bx, bool coupled) {
-    if (bx == 128)
-        return coupled ? TmaLayout<128, true, ST_F32>::bytes : TmaLayout<128, false, ST_F32>::bytes;
-    if (bx == 64)
-        return coupled ? TmaLayout<64, true, ST_F32>::bytes : TmaLayout<64, false, ST_F32>::bytes;
-    return 0;
+namespace {
+
+// Calls f with the block width as a compile-time constant (64, 128 or 192).
+template <typename F>
+auto with_bx(int bx, F&& f) {
+    if (bx == 192) return f(std::integral_constant<int, 192>{});
+    if (bx == 64) return f(std::integral_constant<int, 64>{});
+    return f(std::integral_constant<int, 128>{});
 }
+
+bool bx_supported(int bx) { return bx == 64 || bx == 128 || bx == 192; }
 
 template <int BX, bool COUPLED>
 void set_attr_batch() {
@@ -120,58 +124,57 @@ void set_attr_batch() {
                          (int)TmaLayout<BX, COUPLED, ST_F32>::bytes);
 }
 
+}  // namespace
+
+size_t tma_smem_bytes(int bx, bool coupled) {
+    if (!bx_supported(bx)) return 0;
+    return with_bx(bx, [&](auto B) -> size_t {
+        return coupled ? TmaLayout<B(), true, ST_F32>::bytes : TmaLayout<B(), false, ST_F32>::bytes;
+    });
+}
+
 cudaError_t configure_tma_smem() {
-    set_attr<128, true>();
-    set_attr<128, false>();
-    set_attr<64, true>();
-    set_attr<64, false>();
-    set_attr_batch<128, true>();
-    set_attr_batch<128, false>();
-    set_attr_batch<64, true>();
-    set_attr_batch<64, false>();
+    for (int bx : {64, 128, 192})
+        with_bx(bx, [](auto B) {
+            set_attr<B(), true>();
+            set_attr<B(), false>();
+            set_attr_batch<B(), true>();
+            set_attr_batch<B(), false>();
+            return 0;
+        });
     return cudaGetLastError();
 }
 
 int tma_batch_blocks_per_sm(int bx, bool coupled) {
     int n = 0;
     const size_t smem = tma_smem_bytes(bx, coupled);
-    cudaError_t e;
-    if (bx == 128)
-        e = coupled ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep_tma_batch<128, true>, 256, smem)
-                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep_tma_batch<128, false>, 256, smem);
-    else
-        e = coupled ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep_tma_batch<64, true>, 128, smem)
-                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep_tma_batch<64, false>, 128, smem);
+    const cudaError_t e = with_bx(bx, [&](auto B) {
+        return coupled ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep_tma_batch<B(), true>, 2 * B(), smem)
+                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep_tma_batch<B(), false>, 2 * B(), smem);
+    });
     return e == cudaSuccess && n > 0 ? n : 1;
 }
 
 int tma_blocks_per_sm(int bx, bool coupled) {
     int n = 0;
     const size_t smem = tma_smem_bytes(bx, coupled);
-    cudaError_t e;
-    if (bx == 128)
-        e = coupled ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep_tma<128, true>, 256, smem)
-                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep_tma<128, false>, 256, smem);
-    else
-        e = coupled ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep_tma<64, true>, 128, smem)
-                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep_tma<64, false>, 128, smem);
+    const cudaError_t e = with_bx(bx, [&](auto B) {
+        return coupled ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep_tma<B(), true>, 2 * B(), smem)
+                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep_tma<B(), false>, 2 * B(), smem);
+    });
     return e == cudaSuccess && n > 0 ? n : 1;
 }
 
 void launch_step_tma_batch(const RunDesc* runs, const int4* items, int nitems, int blocks,
                            int bx, bool coupled, int src, int* err, cudaStream_t st) {
     const size_t smem = tma_smem_bytes(bx, coupled);
-    if (bx == 128) {
+    with_bx(bx, [&](auto B) {
         if (coupled)
-            k_sweep_tma_batch<128, true><<<blocks, 256, smem, st>>>(runs, items, nitems, src, err);
+            k_sweep_tma_batch<B(), true><<<blocks, 2 * B(), smem, st>>>(runs, items, nitems, src, err);
         else
-            k_sweep_tma_batch<128, false><<<blocks, 256, smem, st>>>(runs, items, nitems, src, err);
-    } else {
-        if (coupled)
-            k_sweep_tma_batch<64, true><<<blocks, 128, smem, st>>>(runs, items, nitems, src, err);
-        else
-            k_sweep_tma_batch<64, false><<<blocks, 128, smem, st>>>(runs, items, nitems, src, err);
-    }
+            k_sweep_tma_batch<B(), false><<<blocks, 2 * B(), smem, st>>>(runs, items, nitems, src, err);
+        return 0;
+    });
 }
 
 void launch_step_tma(const KParams& p, const DevState& s, int src, const FusedShape& sh,
@@ -180,17 +183,13 @@ void launch_step_tma(const KParams& p, const DevState& s, int src, const FusedSh
     dim3 grid((p.nx + tx - 1) / tx, (p.ny + sh.seg - 1) / sh.seg);
     const size_t smem = tma_smem_bytes(sh.bx, p.coupled);
     float* dst = s.pop[1 - src];
-    if (sh.bx == 128) {
+    with_bx(sh.bx, [&](auto B) {
         if (p.coupled)
-            k_sweep_tma<128, true><<<grid, 256, smem, st>>>(maps[src], p, dst, s.fields, sh.seg, err);
+            k_sweep_tma<B(), true><<<grid, 2 * B(), smem, st>>>(maps[src], p, dst, s.fields, sh.seg, err);
         else
-            k_sweep_tma<128, false><<<grid, 256, smem, st>>>(maps[src], p, dst, s.fields, sh.seg, err);
-    } else {
-        if (p.coupled)
-            k_sweep_tma<64, true><<<grid, 128, smem, st>>>(maps[src], p, dst, s.fields, sh.seg, err);
-        else
-            k_sweep_tma<64, false><<<grid, 128, smem, st>>>(maps[src], p, dst, s.fields, sh.seg, err);
-    }
+            k_sweep_tma<B(), false><<<grid, 2 * B(), smem, st>>>(maps[src], p, dst, s.fields, sh.seg, err);
+        return 0;
+    });
 }
 
 }  // namespace lbm

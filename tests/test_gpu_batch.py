@@ -37,7 +37,7 @@ def init_all(sims, cases):
         s.init(c.phi, c.c, c.ux, c.uy, c.P)
 
 
-@pytest.mark.parametrize("shape", [(128, 32), (64, 16)])
+@pytest.mark.parametrize("shape", [(128, 32), (64, 16), (192, 24)])
 def test_batch_bitwise_equals_single_runs(shape):
     cases = mixed_cases()
     b = lbm.Batch([c.phys for c in cases])
@@ -94,7 +94,7 @@ def test_run_stepped_alone_rejoins_batch():
 def test_batch_launch_shape_and_tiles():
     cases = mixed_cases()
     b = lbm.Batch([c.phys for c in cases])
-    for tx, seg in ((128, 32), (64, 48), (128, 4)):
+    for tx, seg in ((128, 32), (64, 48), (128, 4), (192, 16)):
         b.set_launch_shape(tx, seg)
         bx, sy, blocks, tiles = b.launch_shape()
         expect = sum(-(-c.phys.nx // (tx - 4)) * -(-c.phys.ny // seg) for c in cases)
@@ -139,7 +139,7 @@ def test_autotune_single_restores_state():
     s.step(7)
     before = s.fields()
     tx, seg, ms = s.autotune(steps=8)
-    assert tx in (64, 128) and seg >= 4 and ms > 0
+    assert tx in (64, 128, 192) and seg >= 4 and ms > 0
     assert lbm.lbm_get_launch_shape(s.ctx) == (tx, seg)
     assert s.t == 7
     after = s.fields()
@@ -162,7 +162,7 @@ def test_batch_autotune_restores_state():
     b.sync()
     before = [r.fields() for r in b.runs]
     tx, seg, ms = b.autotune(steps=4)
-    assert tx in (64, 128) and seg >= 4 and ms > 0
+    assert tx in (64, 128, 192) and seg >= 4 and ms > 0
     assert b.launch_shape()[:2] == (tx, seg)
     assert [r.t for r in b.runs] == [5] * len(cases)
     for r, f0 in zip(b.runs, before):

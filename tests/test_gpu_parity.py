@@ -135,7 +135,7 @@ def test_sweeps_match_split(kernel):
         assert np.abs(a[k] - b[k]).max() < 1e-6, k
 
 
-@pytest.mark.parametrize("shape", [(64, 8), (64, 5), (128, 4), (128, 37)])
+@pytest.mark.parametrize("shape", [(64, 8), (64, 5), (128, 4), (128, 37), (192, 6), (192, 40)])
 def test_tma_launch_shapes(shape):
     """Every block width and segment height of the TMA sweep, on ragged grids
     with walls and periodic y, reproduces the three-kernel chain."""
