@@ -190,8 +190,9 @@ int lbm_kernel_in_use(const lbm_ctx *ctx);
 int lbm_launches_per_step(const lbm_ctx *ctx);
 
 /* Launch shape of the sweep kernels: threads per block (tile_x; the block
- * owns tile_x - 4 columns; 128 for FUSED and for TMA with 16-bit storage;
- * 64, 128 or 192 for TMA with FP32 storage) and rows per block (seg_y >= 4).
+ * owns tile_x - 4 columns; 128 for FUSED; 128 or 192 for TMA with 16-bit
+ * storage; 64, 128 or 192 for TMA with FP32 storage) and rows per block
+ * (seg_y >= 4).
  * 0 keeps the current value.
  * Errors: INVALID_ARG, UNSUPPORTED (split kernel, or tile_x not available). */
 int lbm_set_launch_shape(lbm_ctx *ctx, int32_t tile_x, int32_t seg_y);
@@ -217,8 +218,8 @@ int lbm_debug_stall_next_step(lbm_ctx *ctx);
  * per block seg_y) over `steps` steps of the live state (after 2 warm-up
  * steps, CUDA events on the context's stream), restores the state, step count
  * and buffer parity after each candidate, and keeps the fastest shape.
- * Candidates: tile_x in {128, 192, 64} (TMA kernel with FP32 storage; 128
- * only for FUSED and 16-bit storage), seg_y in
+ * Candidates: tile_x in {128, 192, 64} (TMA kernel with FP32 storage;
+ * {128, 192} with 16-bit storage; 128 for FUSED), seg_y in
  * {8, 16, 32, 64, 128} plus the values that fill one and two waves of
  * resident blocks.  Needs one extra device buffer the size of a population
  * buffer while it runs.  Outputs (nullable): chosen shape and its time per

@@ -637,9 +637,9 @@ int lbm_set_launch_shape(lbm_ctx* ctx, int32_t tile_x, int32_t seg_y) {
     if (tile_x < 0 || (tile_x != 0 && (tile_x % 32 != 0 || tile_x < 64 || tile_x > 512)))
         return LBM_ERR_INVALID_ARG;
     if (seg_y != 0 && seg_y < 4) return LBM_ERR_INVALID_ARG;
-    const bool ok_bx = tile_x == 0 || tile_x == 128 ||
-                       ((tile_x == 64 || tile_x == 192) && ctx->kernel == LBM_KERNEL_TMA &&
-                        ctx->st == lbm::ST_F32);
+    const bool tma = ctx->kernel == LBM_KERNEL_TMA;
+    const bool ok_bx = tile_x == 0 || tile_x == 128 || (tile_x == 192 && tma) ||
+                       (tile_x == 64 && tma && ctx->st == lbm::ST_F32);
     if (!ok_bx) return LBM_ERR_UNSUPPORTED;
     if (tile_x) ctx->shape.bx = tile_x;
     if (seg_y) ctx->shape.seg = seg_y;
@@ -1197,11 +1197,11 @@ int lbm_autotune(lbm_ctx* ctx, int32_t steps, int32_t* tile_x, int32_t* seg_y,
     double best = 1e300;
     lbm::FusedShape best_shape = shape0;
     const int bxs[3] = {128, 192, 64};
-    const int nbx = ctx->kernel == LBM_KERNEL_TMA && ctx->st == lbm::ST_F32 ? 3 : 1;
+    const int nbx = ctx->kernel != LBM_KERNEL_TMA ? 1 : ctx->st == lbm::ST_F32 ? 3 : 2;
     for (int a = 0; a < nbx && ce == cudaSuccess && rc == LBM_OK; ++a) {
         const int bx = bxs[a];
         const int per_sm = ctx->kernel != LBM_KERNEL_TMA ? 2
-                           : ctx->st != lbm::ST_F32   ? lbm::tma16_blocks_per_sm(ctx->kp.coupled, ctx->st)
+                           : ctx->st != lbm::ST_F32   ? lbm::tma16_blocks_per_sm(bx, ctx->kp.coupled, ctx->st)
                                                       : lbm::tma_blocks_per_sm(bx, ctx->kp.coupled);
         int segs[8];
         const int ns = seg_candidates(ctx->kp.nx, ctx->kp.ny, bx, per_sm, segs, 8);

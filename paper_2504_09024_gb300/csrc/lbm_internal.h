@@ -55,12 +55,12 @@ void launch_step_tma_batch(const RunDesc* runs, const int4* items, int nitems, i
                            int bx, bool coupled, int src, int* err, cudaStream_t st);
 int tma_batch_blocks_per_sm(int bx, bool coupled);
 int tma_blocks_per_sm(int bx, bool coupled);
-// Fused TMA step with 16-bit storage (lbm_sweep_tma16.cu; block width 128).
+// Fused TMA step with 16-bit storage (lbm_sweep_tma16.cu; block width 128 or 192).
 // st: ST_F16 or ST_BF16 (lbm_store16.cuh); buffers hold store_planes(st, .)
 // word planes, pointers to column 0 like the FP32 ones.
-size_t tma16_smem_bytes(bool coupled);
+size_t tma16_smem_bytes(int bx, bool coupled);
 cudaError_t configure_tma16_smem();
-int tma16_blocks_per_sm(bool coupled, int st);
+int tma16_blocks_per_sm(int bx, bool coupled, int st);
 void launch_step_tma16(const KParams& p, float* src16, float* dst16, const float* fields,
                        const FusedShape& sh, const CUtensorMap& map, int st, int* err,
                        cudaStream_t s);

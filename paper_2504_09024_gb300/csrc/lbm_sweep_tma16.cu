@@ -8,24 +8,25 @@
 // differ.  Whole-buffer packing (initialisation, set_populations) rounds to
 // nearest.
 #include <cudaTypedefs.h>
+#include <type_traits>
 
 #include "lbm_sweep_tile.cuh"
 
 namespace lbm {
 
-template <bool COUPLED, int ST>
-__global__ void __launch_bounds__(256, tma_min_blocks<128>()) k_sweep_tma16(
+template <int BX, bool COUPLED, int ST>
+__global__ void __launch_bounds__(2 * BX, tma_min_blocks<BX>()) k_sweep_tma16(
     const __grid_constant__ CUtensorMap tmap, KParams p, float* __restrict__ dst,
     const float* __restrict__ F, int seg, int* __restrict__ err) {
     extern __shared__ unsigned char smem_raw[];
-    const TmaSmem<128, COUPLED, ST> S(smem_raw);
+    const TmaSmem<BX, COUPLED, ST> S(smem_raw);
     if (threadIdx.x == 0) {
         for (int k = 0; k <= TMA_STAGES; ++k) mbar_init(&S.bars[k], 1);  // [TMA_STAGES]: test hook
         fence_barrier_init();
     }
     __syncthreads();
     uint32_t issued = 0;
-    sweep_tile<128, COUPLED, ST>(&tmap, p, dst, F, seg, blockIdx.x, blockIdx.y, S, issued, err);
+    sweep_tile<BX, COUPLED, ST>(&tmap, p, dst, F, seg, blockIdx.x, blockIdx.y, S, issued, err);
 }
 
 // FP32 deviation-form buffer (27 or 18 float planes) -> 16-bit words (15 or
@@ -82,50 +83,66 @@ __global__ void k_step_advance(unsigned* ctr, unsigned n) { *ctr += n; }
 // host side
 // ---------------------------------------------------------------------------
 
-size_t tma16_smem_bytes(bool coupled) {
-    return coupled ? TmaLayout<128, true, ST_F16>::bytes : TmaLayout<128, false, ST_F16>::bytes;
+namespace {
+
+// Calls f with the block width (128 or 192) and the storage format as
+// compile-time constants.
+template <typename F>
+auto with_bx_st(int bx, int st, F&& f) {
+    if (bx == 192)
+        return st == ST_F16 ? f(std::integral_constant<int, 192>{}, std::integral_constant<int, ST_F16>{})
+                            : f(std::integral_constant<int, 192>{}, std::integral_constant<int, ST_BF16>{});
+    return st == ST_F16 ? f(std::integral_constant<int, 128>{}, std::integral_constant<int, ST_F16>{})
+                        : f(std::integral_constant<int, 128>{}, std::integral_constant<int, ST_BF16>{});
+}
+
+}  // namespace
+
+size_t tma16_smem_bytes(int bx, bool coupled) {
+    if (bx != 128 && bx != 192) return 0;
+    // FP16 and BF16 words have the same layout
+    return with_bx_st(bx, ST_F16, [&](auto B, auto) -> size_t {
+        return coupled ? TmaLayout<B(), true, ST_F16>::bytes : TmaLayout<B(), false, ST_F16>::bytes;
+    });
 }
 
 cudaError_t configure_tma16_smem() {
-    const int b1 = (int)tma16_smem_bytes(true), b0 = (int)tma16_smem_bytes(false);
-    cudaFuncSetAttribute(k_sweep_tma16<true, ST_F16>, cudaFuncAttributeMaxDynamicSharedMemorySize, b1);
-    cudaFuncSetAttribute(k_sweep_tma16<false, ST_F16>, cudaFuncAttributeMaxDynamicSharedMemorySize, b0);
-    cudaFuncSetAttribute(k_sweep_tma16<true, ST_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, b1);
-    cudaFuncSetAttribute(k_sweep_tma16<false, ST_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, b0);
+    for (int bx : {128, 192})
+        for (int st : {ST_F16, ST_BF16})
+            with_bx_st(bx, st, [&](auto B, auto S) {
+                cudaFuncSetAttribute(k_sweep_tma16<B(), true, S()>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)tma16_smem_bytes(B(), true));
+                cudaFuncSetAttribute(k_sweep_tma16<B(), false, S()>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)tma16_smem_bytes(B(), false));
+                return 0;
+            });
     return cudaGetLastError();
 }
 
-int tma16_blocks_per_sm(bool coupled, int st) {
+int tma16_blocks_per_sm(int bx, bool coupled, int st) {
     int n = 0;
-    const size_t smem = tma16_smem_bytes(coupled);
-    cudaError_t e;
-    if (st == ST_F16)
-        e = coupled ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep_tma16<true, ST_F16>, 256, smem)
-                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep_tma16<false, ST_F16>, 256, smem);
-    else
-        e = coupled ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep_tma16<true, ST_BF16>, 256, smem)
-                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep_tma16<false, ST_BF16>, 256, smem);
+    const size_t smem = tma16_smem_bytes(bx, coupled);
+    const cudaError_t e = with_bx_st(bx, st, [&](auto B, auto S) {
+        return coupled ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep_tma16<B(), true, S()>, 2 * B(), smem)
+                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep_tma16<B(), false, S()>, 2 * B(), smem);
+    });
     return e == cudaSuccess && n > 0 ? n : 1;
 }
 
 void launch_step_tma16(const KParams& p, float* src16, float* dst16, const float* fields,
                        const FusedShape& sh, const CUtensorMap& map, int st, int* err,
                        cudaStream_t s) {
-    const int tx = 128 - 4;
+    const int tx = sh.bx - 4;
     dim3 grid((p.nx + tx - 1) / tx, (p.ny + sh.seg - 1) / sh.seg);
-    const size_t smem = tma16_smem_bytes(p.coupled);
+    const size_t smem = tma16_smem_bytes(sh.bx, p.coupled);
     (void)src16;
-    if (st == ST_F16) {
+    with_bx_st(sh.bx, st, [&](auto B, auto S) {
         if (p.coupled)
-            k_sweep_tma16<true, ST_F16><<<grid, 256, smem, s>>>(map, p, dst16, fields, sh.seg, err);
+            k_sweep_tma16<B(), true, S()><<<grid, 2 * B(), smem, s>>>(map, p, dst16, fields, sh.seg, err);
         else
-            k_sweep_tma16<false, ST_F16><<<grid, 256, smem, s>>>(map, p, dst16, fields, sh.seg, err);
-    } else {
-        if (p.coupled)
-            k_sweep_tma16<true, ST_BF16><<<grid, 256, smem, s>>>(map, p, dst16, fields, sh.seg, err);
-        else
-            k_sweep_tma16<false, ST_BF16><<<grid, 256, smem, s>>>(map, p, dst16, fields, sh.seg, err);
-    }
+            k_sweep_tma16<B(), false, S()><<<grid, 2 * B(), smem, s>>>(map, p, dst16, fields, sh.seg, err);
+        return 0;
+    });
 }
 
 void launch_step_advance(unsigned* ctr, unsigned n, cudaStream_t s) {
