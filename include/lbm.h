@@ -101,11 +101,12 @@ typedef struct lbm_diag {
     int64_t step;            /* time steps taken since the last initialisation */
     double sum_phi, sum_c;   /* FP64 totals of phi and c over the grid */
     double D, L, B;          /* deformation D = (L - B)/(L + B) (Sec. 4.3, Fig. 8): L = 4 sqrt(l1),
-                                B = 4 sqrt(l2) from the phi-weighted second moments */
-    double xc, yc;           /* phi-weighted centroid (circular mean on periodic axes) */
+                                B = 4 sqrt(l2) from the second moments of the drop
+                                indicator w = clip((phi - phi_b) / (phi_a - phi_b), 0, 1) */
+    double xc, yc;           /* w-weighted centroid (circular mean on periodic axes) */
     double umax;             /* max |u| */
     int64_t nonfinite;       /* cells with a non-finite phi, c or u */
-    int64_t sigma_neg;       /* cells where 1 + beta ln(1 - c / c_max) < 0 (Eq. EOS) */
+    int64_t sigma_neg;       /* cells where 1 + beta ln(1 - c / c_max) < 0 (Eq. EOS); 0 when beta = 0 */
     int32_t status;          /* LBM_OK, or LBM_ERR_NONFINITE when nonfinite > 0 */
     int32_t reserved;
 } lbm_diag;
@@ -335,7 +336,8 @@ int surr_train(surr_ctx *ctx, const float *X, const float *yD, const float *yB, 
  * result: device array of LBM_FIELD_STATS_LEN doubles, written in full:
  *   [0] sum phi  [1] sum c  [2] xc  [3] yc  [4] non-finite cells
  *   [5] cells with sigma < 0  [6] max |u|  [7] Ixx  [8] Iyy  [9] Ixy
- *   [10] L  [11] B  [12] D   (moments, L, B, D as in lbm_diag)
+ *   [10] L  [11] B  [12] D   (moments, L, B, D as in lbm_diag, of the drop
+ *   indicator clip(phi, 0, 1): phases phi_a = 1 and phi_b = 0)
  * stream: cudaStream_t to run on (NULL: the legacy default stream).
  * Asynchronous on `stream`.  The first call on a device looks up the device
  * address of the scratch array (cudaGetSymbolAddress) with that device

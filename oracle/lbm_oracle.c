@@ -303,8 +303,11 @@ static double lin_interp(const orc_params *p, double phi, double va, double vb) 
     return vb + (phi - p->phi_b) / (p->phi_a - p->phi_b) * (va - vb);
 }
 
-/* Langmuir equation of state, Eq. (EOS). */
+/* Langmuir equation of state, Eq. (EOS).  With beta = 0 (a clean interface)
+ * the tension is sigma_o whatever c is: the logarithm is not formed, so a
+ * passive surfactant that reaches c_max leaves the tension defined. */
 static double sigma_of_c(const orc_params *p, double c) {
+    if (p->beta == 0.0) return p->sigma_o;
     return p->sigma_o * (1.0 + p->beta * log(1.0 - c / p->c_max));
 }
 
@@ -705,6 +708,16 @@ void orc_set_pops(orc_sim *s, const double *f, const double *h, const double *g)
 
 /* Periodic-aware centroid along one axis: circular mean of the phi-weighted
  * positions when the axis is periodic, plain mean otherwise. */
+/* Phase indicator of the drop: (phi - phi_b) / (phi_a - phi_b) clipped to
+ * [0, 1].  The drop's axes L and B (Sec. 4.3, D = (L - B) / (L + B)) belong to
+ * the drop region; the clip keeps the small overshoot and undershoot of phi
+ * away from the interface out of the shape moments, where their distance
+ * from the drop would weigh them heavily. */
+static double drop_indicator(const orc_params *p, double phi) {
+    double w = (phi - p->phi_b) / (p->phi_a - p->phi_b);
+    return w < 0.0 ? 0.0 : (w > 1.0 ? 1.0 : w);
+}
+
 static double axis_centroid(const orc_sim *s, int axis, int periodic) {
     const orc_params *p = &s->p;
     int nx = p->nx, ny = p->ny, n = axis == 0 ? nx : ny;
@@ -714,15 +727,16 @@ static double axis_centroid(const orc_sim *s, int axis, int periodic) {
             size_t x = (size_t)j * nx + i;
             double phi = s->phi[x];
             if (!isfinite(phi)) continue;
+            double w = drop_indicator(p, phi);
             double pos = (axis == 0 ? i : j) + 0.5;
             if (periodic) {
                 double ang = 2.0 * M_PI * pos / n;
-                a += phi * cos(ang);
-                b += phi * sin(ang);
+                a += w * cos(ang);
+                b += w * sin(ang);
             } else {
-                a += phi * pos;
+                a += w * pos;
             }
-            s0 += phi;
+            s0 += w;
         }
     if (s0 == 0) return 0.5 * n;
     if (!periodic) return a / s0;
@@ -738,8 +752,8 @@ static double min_image(double d, int n, int periodic) {
     return d;
 }
 
-/* Sums of phi and c, the phi-weighted centroid and second moments (the drop
- * shape: L = 4 sqrt(l1), B = 4 sqrt(l2), D = (L - B) / (L + B)), max |u|,
+/* Sums of phi and c, the centroid and second moments of the drop indicator
+ * (the drop shape: L = 4 sqrt(l1), B = 4 sqrt(l2), D = (L - B) / (L + B)), max |u|,
  * and counts of non-finite cells and of cells with negative sigma(c).
  * Periodic axes use the circular-mean centroid and minimum-image distances. */
 void orc_diagnostics(orc_sim *s, orc_diag *out) {
@@ -763,25 +777,27 @@ void orc_diagnostics(orc_sim *s, orc_diag *out) {
             double um = sqrt(s->ux[x] * s->ux[x] + s->uy[x] * s->uy[x]);
             if (um > umax) umax = um;
             double arg = 1.0 - c / p->c_max;
-            if (arg <= 0.0 || 1.0 + p->beta * log(arg) < 0.0) neg++;
+            if (p->beta != 0.0 && (arg <= 0.0 || 1.0 + p->beta * log(arg) < 0.0)) neg++;
         }
     double xc = axis_centroid(s, 0, 1), yc = axis_centroid(s, 1, py);
-    double Ixx = 0, Iyy = 0, Ixy = 0;
+    double Ixx = 0, Iyy = 0, Ixy = 0, sw = 0;
     for (int j = 0; j < ny; ++j)
         for (int i = 0; i < nx; ++i) {
             size_t x = (size_t)j * nx + i;
             double phi = s->phi[x];
             if (!isfinite(phi) || !isfinite(s->c[x]) || !isfinite(s->ux[x]) || !isfinite(s->uy[x]))
                 continue;
+            double w = drop_indicator(p, phi);
             double dx = min_image(i + 0.5 - xc, nx, 1), dy = min_image(j + 0.5 - yc, ny, py);
-            Ixx += phi * dx * dx;
-            Iyy += phi * dy * dy;
-            Ixy += phi * dx * dy;
+            Ixx += w * dx * dx;
+            Iyy += w * dy * dy;
+            Ixy += w * dx * dy;
+            sw += w;
         }
-    if (s0 != 0) {
-        Ixx /= s0;
-        Iyy /= s0;
-        Ixy /= s0;
+    if (sw != 0) {
+        Ixx /= sw;
+        Iyy /= sw;
+        Ixy /= sw;
     }
     double tr = Ixx + Iyy, det = Ixx * Iyy - Ixy * Ixy;
     double disc = sqrt(fmax(0.25 * tr * tr - det, 0.0));

@@ -330,9 +330,12 @@ __device__ __forceinline__ void unit_normal(float gx, float gy, float& nx, float
     mag = g2 * inv;
 }
 
-// Langmuir isotherm, Eq. (EOS).
+// Langmuir isotherm, Eq. (EOS).  beta = 0 (clean interface) gives sigma_o
+// whatever c is: 0 * log(<= 0) would be NaN once a passive surfactant reaches
+// c_max, so the product is selected away rather than formed.
 __device__ __forceinline__ float sigma_of_c(const KParams& p, float c) {
-    return p.sigma_o * (1.0f + p.beta * __logf(1.0f - c * p.inv_cmax));
+    const float t = p.beta * __logf(1.0f - c * p.inv_cmax);
+    return p.sigma_o * (1.0f + (p.beta != 0.0f ? t : 0.0f));
 }
 
 // ---------------------------------------------------------------------------

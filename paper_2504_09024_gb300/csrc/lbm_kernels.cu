@@ -504,8 +504,18 @@ __device__ void block_sum(double (&v)[NS], double* partial_out) {
     }
 }
 
-// Pass 1 sums: phi, c, phi cos/sin(2 pi x / nx), phi cos/sin(2 pi y / ny),
-// phi y, nonfinite count, sigma<0 count, max |u| (as max), spare.
+// Drop indicator: (phi - phi_b) / (phi_a - phi_b) clipped to [0, 1].  The
+// shape moments (centroid, Ixx, Iyy, Ixy; D = (L - B) / (L + B) of Sec. 4.3)
+// belong to the drop region: the clip keeps the small over- and undershoot of
+// phi away from the interface, which its distance would weigh heavily, out.
+__device__ __forceinline__ double drop_indicator(const KParams& p, double phi) {
+    const double w = (phi - (double)p.phi_b) / ((double)p.phi_a - (double)p.phi_b);
+    return fmin(fmax(w, 0.0), 1.0);
+}
+
+// Pass 1 sums: phi, c, w cos/sin(2 pi x / nx), w cos/sin(2 pi y / ny), w y,
+// nonfinite count, sigma<0 count, max |u| (as max), w (w: drop indicator).
+constexpr int DIAG_SW = 10;  // slot of sum w; after pass 1, block 0's slot holds the total
 __global__ void k_diag1(KParams p, const double* __restrict__ phi, const double* __restrict__ c,
                         const double* __restrict__ ux, const double* __restrict__ uy,
                         double* __restrict__ partial) {
@@ -522,15 +532,17 @@ __global__ void k_diag1(KParams p, const double* __restrict__ phi, const double*
             continue;
         }
         const double ax = TWO_PI * (i + 0.5) / p.nx, ay = TWO_PI * (j + 0.5) / p.ny;
+        const double w = drop_indicator(p, f);
         v[0] += f;
         v[1] += cc;
-        v[2] += f * cos(ax);
-        v[3] += f * sin(ax);
-        v[4] += f * cos(ay);
-        v[5] += f * sin(ay);
-        v[6] += f * (j + 0.5);
+        v[2] += w * cos(ax);
+        v[3] += w * sin(ax);
+        v[4] += w * cos(ay);
+        v[5] += w * sin(ay);
+        v[6] += w * (j + 0.5);
+        v[DIAG_SW] += w;
         const double arg = 1.0 - cc * (double)p.inv_cmax;
-        if (arg <= 0.0 || 1.0 + (double)p.beta * log(arg) < 0.0) v[8] += 1.0;
+        if (p.beta != 0.0f && (arg <= 0.0 || 1.0 + (double)p.beta * log(arg) < 0.0)) v[8] += 1.0;
         umax = fmax(umax, sqrt(a * a + b * b));
     }
     for (int o = 16; o > 0; o >>= 1) umax = fmax(umax, __shfl_down_sync(0xffffffffu, umax, o));
@@ -546,7 +558,7 @@ __global__ void k_diag1(KParams p, const double* __restrict__ phi, const double*
 
 // result layout: [0] sum_phi [1] sum_c [2] xc [3] yc [4] nonfinite [5] sigma_neg [6] umax
 //                [7] Ixx [8] Iyy [9] Ixy [10] L [11] B [12] D
-__global__ void k_diag_finish1(KParams p, const double* __restrict__ partial, int nb,
+__global__ void k_diag_finish1(KParams p, double* __restrict__ partial, int nb,
                                double* __restrict__ res) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     double s[DIAG_NSUM];
@@ -560,12 +572,12 @@ __global__ void k_diag_finish1(KParams p, const double* __restrict__ partial, in
     res[0] = s[0];
     res[1] = s[1];
     double xc = 0.5 * p.nx, yc = 0.5 * p.ny;
-    if (s[0] != 0.0) {
+    if (s[DIAG_SW] != 0.0) {
         double ax = atan2(s[3], s[2]);
         if (ax < 0) ax += TWO_PI;
         xc = ax * p.nx / TWO_PI;
         if (p.walls) {
-            yc = s[6] / s[0];
+            yc = s[6] / s[DIAG_SW];
         } else {
             double ay = atan2(s[5], s[4]);
             if (ay < 0) ay += TWO_PI;
@@ -577,6 +589,8 @@ __global__ void k_diag_finish1(KParams p, const double* __restrict__ partial, in
     res[4] = s[7];
     res[5] = s[8];
     res[6] = m;
+    // the normalisation of pass 2 (the result array has no free slot)
+    partial[DIAG_SW] = s[DIAG_SW];
 }
 
 __device__ __forceinline__ double min_image(double d, int n, bool periodic) {
@@ -599,9 +613,10 @@ __global__ void k_diag2(KParams p, const double* __restrict__ phi, const double*
         if (!finite_cell(f, c[o], ux[o], uy[o])) continue;
         const double dx = min_image(i + 0.5 - xc, p.nx, true);
         const double dy = min_image(j + 0.5 - yc, p.ny, !p.walls);
-        v[0] += f * dx * dx;
-        v[1] += f * dy * dy;
-        v[2] += f * dx * dy;
+        const double w = drop_indicator(p, f);
+        v[0] += w * dx * dx;
+        v[1] += w * dy * dy;
+        v[2] += w * dx * dy;
     }
     block_sum<3>(v, partial + (int64_t)blockIdx.x * DIAG_NSUM);
 }
@@ -611,7 +626,7 @@ __global__ void k_diag_finish2(const double* __restrict__ partial, int nb, doubl
     double I[3] = {0.0, 0.0, 0.0};
     for (int b = 0; b < nb; ++b)
         for (int k = 0; k < 3; ++k) I[k] += partial[(int64_t)b * DIAG_NSUM + k];
-    const double s0 = res[0];
+    const double s0 = partial[DIAG_SW];  // sum of the drop indicator (pass 1)
     if (s0 != 0.0)
         for (int k = 0; k < 3; ++k) I[k] /= s0;
     const double tr = I[0] + I[1], det = I[0] * I[1] - I[2] * I[2];

@@ -67,6 +67,8 @@ extern "C" int lbm_field_stats_noalloc(const double* phi, const double* c, const
     p.walls = walls_y;
     p.beta = (float)beta;
     p.inv_cmax = (float)(1.0 / c_max);
+    p.phi_a = 1.0f;  // the drop indicator of the shape moments: phases 1 and 0
+    p.phi_b = 0.0f;
     const int nb = lbm::diag_blocks(p);
     if (nb > kMaxBlocks) return LBM_ERR_INVALID_ARG;
     lbm::launch_diag(p, phi, c, ux, uy, scratch, nb, result, (cudaStream_t)stream);
