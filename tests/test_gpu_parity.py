@@ -306,3 +306,25 @@ def test_count_components(walls):
         got = s.components(0.5)
         ref = _components_reference(s.fields()["phi"] > 0.5, periodic_y=not walls)
         assert got == ref == len(drops), (name, got, ref)
+
+
+def test_clean_interface_survives_c_max():
+    """beta = 0: sigma = sigma_o for every c (Eq. EOS), so a surfactant level
+    beyond c_max on a clean interface keeps the GPU state finite, as in the
+    oracle."""
+    nx = ny = 48
+    phys = W.Physics(nx=nx, ny=ny, walls_y=0, mode=0, W=4.0, M_phi=0.05, D_s=0.05,
+                     sigma_o=1e-3, beta=0.0, c_max=1.0)
+    phi, _ = W.drop_fields(nx, ny, 12.0, 4.0)
+    c = 1.2 * phi * (1 - phi) * 4
+    z = np.zeros_like(phi)
+    s = lbm.Sim(phys, kernel=lbm.LBM_KERNEL_TMA)
+    s.init(phi, c, z, z)
+    s.step(20)
+    d = s.diagnostics()
+    assert d["nonfinite"] == 0 and d["sigma_neg"] == 0
+    o = oracle.Sim(phys)
+    o.init(phi, c, z, z)
+    o.step(20)
+    g, r = s.fields(), o.fields()
+    assert np.abs(g["phi"] - r["phi"]).max() < 1e-6

@@ -601,6 +601,44 @@ def test_diagnostics_ellipse(oracle_mod):
     assert abs(d["D"] - (a - b) / (a + b)) < 0.01
 
 
+def test_diagnostics_ignore_far_field_undershoot(oracle_mod):
+    """L and B are the axes of the drop (Sec. 4.3): a small negative phi far
+    from the drop, which phi-weighted moments would weigh by its squared
+    distance, leaves the ellipse's D unchanged; the sum of phi still sees it."""
+    nx, ny, a, b = 160, 120, 40.0, 25.0
+    X, Y = W.cell_centres(nx, ny)
+    rr = np.sqrt(((X - nx / 2) / a) ** 2 + ((Y - ny / 2) / b) ** 2)
+    base = np.where(rr < 1.0, 1.0, 0.0)
+    z = np.zeros_like(base)
+    ds = []
+    for offset in (0.0, -1e-3):
+        phi = np.where(rr < 1.0, 1.0, offset)
+        s = oracle_mod.Sim(W.Physics(nx=nx, ny=ny, mode=1))
+        s.init(phi, z, z, z)
+        ds.append(s.diagnostics())
+    assert ds[1]["D"] == pytest.approx(ds[0]["D"], abs=1e-12)
+    assert ds[1]["L"] == pytest.approx(ds[0]["L"], abs=1e-9)
+    assert ds[1]["sum_phi"] < ds[0]["sum_phi"] - 0.5 * 1e-3 * (nx * ny - base.sum())
+
+
+def test_clean_interface_tension_independent_of_c(oracle_mod):
+    """Eq. (EOS) with beta = 0 is sigma_o for every c: a surfactant level at
+    and beyond c_max on a clean interface leaves the state finite, and no cell
+    counts as sigma < 0."""
+    nx = ny = 48
+    phys = W.Physics(nx=nx, ny=ny, walls_y=0, mode=0, W=4.0, M_phi=0.05, D_s=0.05,
+                     sigma_o=1e-3, beta=0.0, c_max=1.0)
+    phi, _ = W.drop_fields(nx, ny, 12.0, 4.0)
+    c = 1.2 * phi * (1 - phi) * 4  # peaks at 1.2 > c_max on the interface
+    z = np.zeros_like(phi)
+    s = oracle_mod.Sim(phys)
+    s.init(phi, c, z, z)
+    s.step(20)
+    d = s.diagnostics()
+    assert d["nonfinite"] == 0 and d["sigma_neg"] == 0
+    assert np.isfinite(s.fields()["P"]).all()
+
+
 def _travelling_wave(oracle_mod, U0, T=400, nx=64, nu=0.05, zeta=0.05):
     eps, cs = 1e-6, math.sqrt(CS2)
     phys = W.Physics(nx=nx, ny=4, walls_y=0, mode=0, nu_a=nu, nu_b=nu, zeta=zeta)
