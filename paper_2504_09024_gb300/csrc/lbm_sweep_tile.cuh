@@ -452,8 +452,9 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap* tmap, const KParam
     return !failed;
 }
 
-// Resident blocks per SM the register budget is set for (shared memory allows
-// three 256-thread blocks of the coupled kernel).
+// Resident blocks per SM the register budget is set for: 768 threads (24
+// warps) per SM at 80 registers, which the coupled kernel's shared memory
+// also allows (three blocks at BX = 128, two at BX = 192).
 template <int BX>
 constexpr int tma_min_blocks() { return 384 / BX; }
 
