@@ -41,18 +41,18 @@ def stone_leal(Ca, beta, Pe, lam=1.0):
     return 3.0 * Ca * b_r / (4.0 + Ca * b_r)
 
 
-def make_cases(H=256, Wd=4.0, Gamma0=0.3, Pe_s=10.0):
+def make_cases(H=256, Wd=4.0, Gamma0=0.3, Pe_s=10.0, betas=BETAS):
     cases = []
     for Ca in TABLE1:
-        for beta in BETAS:
+        for beta in betas:
             cases.append(W.shear_drop(3 * H, H, H / 8.0, Wd, Ca=Ca, beta=beta, Gamma0=Gamma0,
                                       Re=RE, Pe_s=Pe_s, nu=NU,
                                       name=f"table1_Ca{Ca:g}_beta{beta:g}"))
     return cases
 
 
-def run(steps=300000, every=20000, H=256, Wd=4.0, Gamma0=0.3, Pe_s=10.0):
-    cases = make_cases(H, Wd, Gamma0, Pe_s)
+def run(steps=300000, every=20000, H=256, Wd=4.0, Gamma0=0.3, Pe_s=10.0, betas=BETAS):
+    cases = make_cases(H, Wd, Gamma0, Pe_s, betas)
     b = lbm.Batch([c.phys for c in cases])
     for r, c in zip(b.runs, cases):
         r.init(c.phi, c.c, c.ux, c.uy)
@@ -87,10 +87,15 @@ def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--steps", type=int, default=300000)
     ap.add_argument("--every", type=int, default=20000)
+    ap.add_argument("--W", type=float, default=4.0, help="interface width (not stated in the paper)")
+    ap.add_argument("--gamma0", type=float, default=0.3)
+    ap.add_argument("--pe-s", type=float, default=10.0)
+    ap.add_argument("--betas", default="0,0.25")
     ap.add_argument("--out", default="")
     args = ap.parse_args(argv)
-    res = run(args.steps, args.every)
-    print(f"{res['grid']}, {res['steps']} steps ({res['wall_s']:.1f} s on the GPU)")
+    betas = tuple(float(b) for b in args.betas.split(","))
+    res = run(args.steps, args.every, Wd=args.W, Gamma0=args.gamma0, Pe_s=args.pe_s, betas=betas)
+    print(f"{res['grid']}, W = {res['W']:g}, {res['steps']} steps ({res['wall_s']:.1f} s on the GPU)")
     print("   Ca   beta   D (GB300)   drift/interval   D (Table 1)   Stone-Leal")
     for r in res["rows"]:
         print(f"{r['Ca']:6.2f} {r['beta']:5.2f}   {r['D']:.4e}     {r['D_drift_last_interval']:+.1e}"
