@@ -112,6 +112,12 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap* tmap, const KParam
     const int y0 = byi * seg;
     const int y1 = min(y0 + seg, p.ny);
     const int col = x0 - 2 + t;
+    // Column roles: 3 the tile's own columns (collided and stored), 2 the
+    // halo columns whose sigma, P* and normals the stencils of the own columns
+    // read, 1 the outer halo columns whose phi the normals of role 2 read, 0
+    // columns beyond the grid in a ragged last tile.  The moments (A) are
+    // formed in every column; the normals (B) for roles 1-3; the collisions
+    // and stores (C) for role 3 only.
     int role = 0;
     if (col >= x0 && col < xend) role = 3;
     else if (col == x0 - 1 || col == xend) role = 2;
