@@ -129,7 +129,8 @@ int lbm_create(const lbm_params *p, void *stream, lbm_ctx **out);
 void lbm_destroy(lbm_ctx *ctx);
 
 /* Set the state to the discrete equilibria of the given macroscopic fields
- * (host float64 [ny][nx] arrays; P may be NULL for P = rho cs^2): for each
+ * (host float64 [ny][nx] arrays; P may be NULL for the uniform rest pressure
+ * P = cs^2 (rho_a + rho_b) / 2, which is rho cs^2 at equal densities): for each
  * lattice P^-1 F^-1(u) applied to its equilibrium central moments, with
  * theta, theta_c and n from the given phi (Sec. 3, App. C, App. D).  In
  * LBM_FIXED_U mode (ux, uy) is also stored as the prescribed velocity.

@@ -630,8 +630,12 @@ int orc_init(orc_sim *s, const double *phi, const double *c, const double *ux, c
         s->ufy[x] = uy[x];
     }
     init_geometry_from_fields(s);
+    /* Default pressure: uniform, cs2 times the mean of the phase densities (the
+     * fluid at rest; psi = P - rho cs2 then carries the density contrast).  With
+     * equal densities this is rho cs2 everywhere. */
+    const double P_rest = CS2 * 0.5 * (s->p.rho_a + s->p.rho_b);
     for (int x = 0; x < N; ++x) {
-        s->P[x] = P ? P[x] : s->rho[x] * CS2;
+        s->P[x] = P ? P[x] : P_rest;
         s->psi[x] = s->P[x] - s->rho[x] * CS2;
     }
     equilibrium_pops(s, 1, 1, 1);

@@ -339,10 +339,9 @@ __global__ void k_init_fields(KParams p, const double* __restrict__ phi,
     F[FP_SIG * p.plane + idx] = sigma_of_c(p, fc);
     F[FP_UX * p.plane + idx] = (float)ux[o];
     F[FP_UY * p.plane + idx] = (float)uy[o];
-    const double rho = p.rho_uniform ? (double)p.rho_a
-                                     : (double)p.rho_b + ((double)fphi - p.phi_b) * p.inv_dphi *
-                                                             ((double)p.rho_a - p.rho_b);
-    const double Pv = P ? P[o] : rho / 3.0;
+    // default pressure: uniform, the rest pressure P0 = cs2 (rho_a + rho_b) / 2
+    // (with equal densities, rho cs2 everywhere)
+    const double Pv = P ? P[o] : (double)p.P0;
     F[FP_DPS * p.plane + idx] = (float)(Pv - (double)p.P0);
 }
 

@@ -5,6 +5,7 @@ steps with FP32 populations, the bound the method's FP32 target states.  A
 one-step comparison at the full 2048x1024 size starts both sides from the same
 (GPU) state and checks every cell.
 """
+import dataclasses
 import math
 import os
 import tempfile
@@ -400,3 +401,22 @@ def test_surface_diffusion_full_size(Ds):
     # rounding, about 2e-9 relative per step (measured: 6.0e-4, 1.9e-4,
     # 3.3e-5 for D_s = 0.05, 0.1, 0.2)
     assert abs(dc) <= 2.5e-9 * T
+
+
+def test_density_and_viscosity_ratio_two():
+    """The general pressure-based flow step (App. D: rho and nu interpolated
+    linearly in phi, F_p = -grad psi with psi = P* - rho cs2 carrying the
+    cs2 grad rho term) at rho_a / rho_b = 2 and nu_a / nu_b = 2, against the
+    oracle after 500 steps of the lively drop."""
+    case = W.lively_shear_drop()
+    phys = dataclasses.replace(case.phys, rho_a=2.0, rho_b=1.0, nu_a=0.15, nu_b=0.075)
+    s = lbm.Sim(phys, kernel=lbm.LBM_KERNEL_TMA)
+    s.init(case.phi, case.c, case.ux, case.uy)
+    s.step(500)
+    o = oracle.Sim(phys)
+    o.init(case.phi, case.c, case.ux, case.uy)
+    o.step(500)
+    g, r = s.fields(), o.fields()
+    errs = {"phi": rel(g["phi"], r["phi"]), "c": rel(g["c"], r["c"]), "u": rel(umag(g), umag(r))}
+    print("ratio 2:", errs)
+    check_lively(g, r)
