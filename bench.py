@@ -341,6 +341,117 @@ def run_ensemble(args, rank, world, local_rank):
     return 0
 
 
+def timed_regions(step_fn, stream, k, repeats, dist=None):
+    """Times `repeats` regions of exactly k steps with CUDA events on the
+    launching stream, each bracketed by a barrier and device synchronisation;
+    returns the per-region times (ms, max over ranks)."""
+    import torch
+    out = []
+    for _ in range(repeats):
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step_fn(k)
+        e1.record(stream)
+        e1.synchronize()
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        out.append(max_over_ranks(e0.elapsed_time(e1), dist))
+    return out
+
+
+def bench_single(case, dtype, args, stream, dist=None, autotune=True):
+    """One context on the workload: autotuned launch shape, W warm-up steps
+    plus one untimed pass of K steps (it captures the step graphs the timed
+    regions replay), then `repeats` timed regions of K steps.  Returns the
+    context and the per-region times (ms)."""
+    from paper_2504_09024_gb300 import lbm
+    dtype_code = {"f32": lbm.LBM_F32, "f16s": lbm.LBM_F16S, "bf16s": lbm.LBM_BF16S}[dtype]
+    kern = {"auto": lbm.LBM_KERNEL_AUTO, "tma": lbm.LBM_KERNEL_TMA, "fused": lbm.LBM_KERNEL_FUSED,
+            "split": lbm.LBM_KERNEL_SPLIT}[args.kernel]
+    sim = lbm.Sim(case.phys, dtype=dtype_code, kernel=kern, stream=stream.cuda_stream)
+    if args.tile_x or args.seg_y:
+        sim.set_launch_shape(args.tile_x, args.seg_y)
+    sim.init(case.phi, case.c, case.ux, case.uy)
+    tuned = None
+    if autotune and not (args.tile_x or args.seg_y) and sim.kernel != lbm.LBM_KERNEL_SPLIT:
+        # the library's autotuner picks the launch shape on the live state
+        # (and puts the state back) before the warm-up
+        tx, sy, tms = sim.autotune(steps=32)
+        tuned = {"tile_x": tx, "seg_y": sy, "ms_per_step": tms}
+    sim.step(args.warmup)
+    sim.step(args.steps)
+    sim.sync()
+    times = timed_regions(sim.step, stream, args.steps, args.repeats, dist)
+    return sim, times, tuned
+
+
+def kernel_name(sim, dtype):
+    from paper_2504_09024_gb300 import lbm
+    if dtype != "f32":
+        return "k_sweep_tma16"
+    return {lbm.LBM_KERNEL_TMA: "k_sweep_tma", lbm.LBM_KERNEL_FUSED: "k_fused_sweep",
+            lbm.LBM_KERNEL_SPLIT: "k_collide"}[sim.kernel]
+
+
+def roofline(dtype, ncell, ms_step, kname):
+    peak, peak_kind = peaks()
+    bpc = BYTES_PER_CELL[dtype]
+    achieved = bpc * ncell / (ms_step * 1e-3) / 1e9
+    tr = traffic_record(kname)
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "peak_kind": f"{peak_kind} hbm_gbs", "bytes_per_cell": bpc,
+            "traffic": tr["bytes_per_launch"] if tr else None}
+
+
+def ensemble_comparison(args, stream):
+    """The 64-run ensemble (uneven grids) in one batch against the same runs
+    stepped one context at a time; FP32, launch shapes from the autotuners.
+    Returns runs/hour of each form at RUN_STEPS steps per run."""
+    import torch
+    from paper_2504_09024_gb300 import lbm, workloads as W
+    RUN_STEPS = 20000
+    draws = W.ensemble_draws(nruns=64, seed=W.CASE_SEED)
+    cases = [W.ensemble_case(d, steps=RUN_STEPS) for d in draws]
+    ncell = sum(c.phys.nx * c.phys.ny for c in cases)
+    k = 64
+    b = lbm.Batch([c.phys for c in cases], stream=stream.cuda_stream)
+    for r, c in zip(b.runs, cases):
+        r.init(c.phi, c.c, c.ux, c.uy)
+    b.autotune(steps=8)
+    b.step(k)
+    b.sync()
+    t_batch = statistics.median(timed_regions(b.step, stream, k, 3)) / k
+    b.close()
+    # one context at a time: every run's grid on its own (runs of equal grid
+    # size cost the same; each size is timed once on one of its runs)
+    by_grid = {}
+    for c in cases:
+        by_grid.setdefault((c.phys.nx, c.phys.ny), []).append(c)
+    t_seq = 0.0
+    for (nx, ny), cs in by_grid.items():
+        sim = lbm.Sim(cs[0].phys, stream=stream.cuda_stream)
+        sim.init(cs[0].phi, cs[0].c, cs[0].ux, cs[0].uy)
+        sim.autotune(steps=32)
+        sim.step(k)
+        sim.sync()
+        t_one = statistics.median(timed_regions(sim.step, stream, k, 3)) / k
+        t_seq += t_one * len(cs)
+        sim.close()
+    torch.cuda.synchronize()
+    return {"runs": len(cases), "cells_per_step": ncell, "run_steps": RUN_STEPS,
+            "batched": {"mlups": ncell / (t_batch * 1e-3) / 1e6,
+                        "runs_per_hour": len(cases) * 3600.0 / (RUN_STEPS * t_batch * 1e-3)},
+            "one_context_at_a_time": {
+                "mlups": ncell / (t_seq * 1e-3) / 1e6,
+                "runs_per_hour": len(cases) * 3600.0 / (RUN_STEPS * t_seq * 1e-3)},
+            "timing": f"median of 3 regions of {k} steps, CUDA events"}
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     from paper_2504_09024_gb300 import lbm
@@ -358,42 +469,16 @@ def run_ours(args, rank, world, local_rank):
     case = make_case(args.workload)
     nx, ny = case.phys.nx, case.phys.ny
     ncell = nx * ny
-    dtype_code = {"f32": lbm.LBM_F32, "f16s": lbm.LBM_F16S, "bf16s": lbm.LBM_BF16S}[args.dtype]
-    kern = {"auto": lbm.LBM_KERNEL_AUTO, "tma": lbm.LBM_KERNEL_TMA, "fused": lbm.LBM_KERNEL_FUSED,
-            "split": lbm.LBM_KERNEL_SPLIT}[args.kernel]
     stream = torch.cuda.Stream()
-    sim = lbm.Sim(case.phys, dtype=dtype_code, kernel=kern, stream=stream.cuda_stream)
-    if args.tile_x or args.seg_y:
-        sim.set_launch_shape(args.tile_x, args.seg_y)
-    sim.init(case.phi, case.c, case.ux, case.uy)
-    tuned = None
-    if not (args.tile_x or args.seg_y) and lbm.lbm_kernel_in_use(sim.ctx) != lbm.LBM_KERNEL_SPLIT:
-        # the library's autotuner picks the launch shape on the live state
-        # (and puts the state back) before the warm-up
-        tx, sy, tms = sim.autotune(steps=32)
-        tuned = {"tile_x": tx, "seg_y": sy, "ms_per_step": tms}
-    launches = lbm.lbm_launches_per_step(sim.ctx)
-
-    # warm-up (also captures the CUDA graphs)
-    sim.step(args.warmup)
-    sim.sync()
     clocks = ClockSampler(local_rank)
     clocks.start()
     time.sleep(0.3)
-    barrier()
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    sim.step(args.steps)
-    e1.record(stream)
-    e1.synchronize()
-    torch.cuda.synchronize()
-    barrier()
+    sim, times, tuned = bench_single(case, args.dtype, args, stream, dist)
     clk = clocks.stop()
-    ms_max = max_over_ranks(e0.elapsed_time(e1), dist)
-    value = whole_job_mlups(world, ncell, args.steps, ms_max * 1e-3)
-    ms_step = ms_max / args.steps
+    ms_region = statistics.median(times)
+    value = whole_job_mlups(world, ncell, args.steps, ms_region * 1e-3)
+    ms_step = ms_region / args.steps
+    launches = lbm.lbm_launches_per_step(sim.ctx)
 
     # end-to-end through the public API with pinned host buffers: initialise
     # from host fields, run the same number of steps, read fields + diagnostics
@@ -413,14 +498,7 @@ def run_ours(args, rank, world, local_rank):
     h2d = sum(a.numel() * 8 for a in host_in)
     d2h = sum(a.numel() * 8 for a in host_out) + 128
 
-    peak, peak_kind = peaks()
-    bpc = BYTES_PER_CELL[args.dtype]
-    achieved = bpc * ncell / (ms_step * 1e-3) / 1e9
-    kname = {lbm.LBM_KERNEL_TMA: "k_sweep_tma", lbm.LBM_KERNEL_FUSED: "k_fused_sweep",
-             lbm.LBM_KERNEL_SPLIT: "k_collide"}[lbm.lbm_kernel_in_use(sim.ctx)]
-    if args.dtype != "f32":
-        kname = "k_sweep_tma16"
-    tr = traffic_record(kname)
+    kname = kernel_name(sim, args.dtype)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
@@ -429,12 +507,13 @@ def run_ours(args, rank, world, local_rank):
                    "lattices": "f+h+g coupled", "kernel": kname,
                    "launch_shape": list(lbm.lbm_get_launch_shape(sim.ctx)),
                    "launch_shape_from": "lbm_autotune" if tuned else "command line",
+                   "timed_regions": f"median of {args.repeats} regions of {args.steps} steps "
+                                    f"({', '.join(f'{t / args.steps * 1e3:.2f}' for t in times)} "
+                                    f"us/step); W warm-up steps and one untimed {args.steps}-step "
+                                    f"pass before them",
                    "l2": "populations (2 x 226 MB) exceed the 129 MB L2; no flush",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "peak_kind": f"{peak_kind} hbm_gbs",
-                     "bytes_per_cell": bpc,
-                     "traffic": tr["bytes_per_launch"] if tr else None},
+        "roofline": roofline(args.dtype, ncell, ms_step, kname),
         "e2e": {"value": whole_job_mlups(world, ncell, args.steps, e2e_s), "unit": UNIT,
                 "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
                 "what": "lbm_init_fields from pinned host fields + lbm_step(K) + lbm_get_fields "
@@ -443,9 +522,21 @@ def run_ours(args, rank, world, local_rank):
         "clocks": clk,
         "check": {"sum_phi": diag["sum_phi"], "nonfinite": diag["nonfinite"]},
     }
+    sim.close()
+    if rank == 0 and world == 1 and args.dtype == "f32" and not args.no_extras:
+        # the same workload with 16-bit storage, and the batched ensemble
+        # against one context at a time (extra keys of the same line)
+        for dt in ("f16s", "bf16s"):
+            s16, t16, _ = bench_single(case, dt, args, stream)
+            ms16 = statistics.median(t16) / args.steps
+            line[dt] = {"value": ncell / (ms16 * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": ms16,
+                        "launch_shape": list(lbm.lbm_get_launch_shape(s16.ctx)),
+                        "vs_f32": ms_step / ms16,
+                        "roofline": roofline(dt, ncell, ms16, "k_sweep_tma16")}
+            s16.close()
+        line["ensemble64"] = ensemble_comparison(args, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(case, args.cpu_budget)
-    sim.close()
     if rank == 0:
         print(json.dumps(line))
     if dist is not None:
@@ -456,8 +547,8 @@ def run_ours(args, rank, world, local_rank):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20000)
-    ap.add_argument("--warmup", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="2048x1024")
     ap.add_argument("--dtype", choices=["f32", "f16s", "bf16s"], default="f32")
@@ -467,6 +558,10 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-budget", type=float, default=90.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="leave out the 16-bit and ensemble keys of the default line")
+    ap.add_argument("--repeats", type=int, default=5,
+                    help="timed regions of K steps; the median is reported")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

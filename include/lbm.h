@@ -145,8 +145,10 @@ int lbm_init_fields_device(lbm_ctx *ctx, const double *phi, const double *c, con
                            const double *uy, const double *P);
 
 /* Advance nsteps >= 0 time steps: stream, moments, interface geometry,
- * forces, and the three central-moment collisions.  Asynchronous.  Long runs
- * replay a captured CUDA graph. */
+ * forces, and the three central-moment collisions.  Asynchronous.  Steps are
+ * replayed from captured CUDA graphs of 32, 16, 8, 4, 2 and 1 steps (largest
+ * first); the first use of a graph captures it (host work, no device
+ * allocation beyond the graph's own). */
 int lbm_step(lbm_ctx *ctx, int64_t nsteps);
 
 /* Macroscopic fields of the current state into host float64 [ny][nx]

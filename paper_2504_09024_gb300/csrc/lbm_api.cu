@@ -19,6 +19,10 @@ cudaError_t configure_fused_smem();
 namespace {
 
 constexpr int GRAPH_STEPS = 32;  // steps per captured graph (even: parity preserved)
+// A single run replays any step count from captured graphs of 32, 16, 8, 4, 2
+// and 1 steps (largest first), so short and long step counts take the same
+// launch path; each chunk size has one graph per buffer parity.
+constexpr int GRAPH_CHUNKS = 6;
 constexpr int BATCH_SIDE_STREAMS = 16;  // concurrent run chains in a batch's graph
 
 }  // namespace
@@ -42,7 +46,7 @@ struct lbm_ctx {
     double* dpartial = nullptr;
     double* dresult = nullptr;
     int diag_nb = 0;
-    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    cudaGraphExec_t graph[GRAPH_CHUNKS][2] = {};  // [log2(32 / steps)][parity]
     CUtensorMap tmaps[2];   // bulk-tensor maps over the two population buffers
     // 16-bit storage: the state lives in pop16 (word planes, lbm_store16.cuh);
     // the FP32 buffers stage initialisation and field output
@@ -64,11 +68,12 @@ int cuda_fail(lbm_ctx* ctx, cudaError_t e) {
 int check_launch(lbm_ctx* ctx) { return cuda_fail(ctx, cudaGetLastError()); }
 
 void drop_graphs(lbm_ctx* ctx) {
-    for (int k = 0; k < 2; ++k)
-        if (ctx->graph[k]) {
-            cudaGraphExecDestroy(ctx->graph[k]);
-            ctx->graph[k] = nullptr;
-        }
+    for (int c = 0; c < GRAPH_CHUNKS; ++c)
+        for (int k = 0; k < 2; ++k)
+            if (ctx->graph[c][k]) {
+                cudaGraphExecDestroy(ctx->graph[c][k]);
+                ctx->graph[c][k] = nullptr;
+            }
 }
 
 int ensure_stage(lbm_ctx* ctx, size_t bytes) {
@@ -239,19 +244,21 @@ int fp32_view(lbm_ctx* ctx) {
     return 0;
 }
 
-int build_graph(lbm_ctx* ctx, int parity) {
+// Graph of GRAPH_STEPS >> chunk steps starting from buffer `parity`.
+int build_graph(lbm_ctx* ctx, int parity, int chunk) {
+    const int n = GRAPH_STEPS >> chunk;
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(ctx, e);
     int src = parity;
-    for (int s = 0; s < GRAPH_STEPS; ++s) {
+    for (int s = 0; s < n; ++s) {
         launch_one_step(ctx, src, ctx->cap_stream, s);
         src ^= 1;
     }
-    if (ctx->dstep) lbm::launch_step_advance(ctx->dstep, GRAPH_STEPS, ctx->cap_stream);
+    if (ctx->dstep) lbm::launch_step_advance(ctx->dstep, n, ctx->cap_stream);
     e = cudaStreamEndCapture(ctx->cap_stream, &g);
     if (e != cudaSuccess) return cuda_fail(ctx, e);
-    e = cudaGraphInstantiate(&ctx->graph[parity], g, 0);
+    e = cudaGraphInstantiate(&ctx->graph[chunk][parity], g, 0);
     cudaGraphDestroy(g);
     return cuda_fail(ctx, e);
 }
@@ -438,15 +445,19 @@ int lbm_init_fields(lbm_ctx* ctx, const double* phi, const double* c, const doub
 int lbm_step(lbm_ctx* ctx, int64_t nsteps) {
     if (!ctx || nsteps < 0) return LBM_ERR_INVALID_ARG;
     while (nsteps > 0) {
-        if (nsteps >= GRAPH_STEPS && !ctx->kp.stall_test) {
-            if (!ctx->graph[ctx->cur]) {
-                int rc = build_graph(ctx, ctx->cur);
+        if (!ctx->kp.stall_test) {
+            int chunk = 0;
+            while ((GRAPH_STEPS >> chunk) > nsteps) ++chunk;
+            const int n = GRAPH_STEPS >> chunk;
+            if (!ctx->graph[chunk][ctx->cur]) {
+                int rc = build_graph(ctx, ctx->cur, chunk);
                 if (rc != LBM_OK) return rc;
             }
-            if (cudaGraphLaunch(ctx->graph[ctx->cur], ctx->stream) != cudaSuccess)
+            if (cudaGraphLaunch(ctx->graph[chunk][ctx->cur], ctx->stream) != cudaSuccess)
                 return cuda_fail(ctx, cudaGetLastError());
-            ctx->step += GRAPH_STEPS;
-            nsteps -= GRAPH_STEPS;
+            ctx->cur ^= n & 1;
+            ctx->step += n;
+            nsteps -= n;
         } else {
             launch_one_step(ctx, ctx->cur, ctx->stream);
             if (ctx->dstep) lbm::launch_step_advance(ctx->dstep, 1, ctx->stream);
@@ -1208,7 +1219,9 @@ int lbm_autotune(lbm_ctx* ctx, int32_t steps, int32_t* tile_x, int32_t* seg_y,
         for (int k = 0; k < ns && rc == LBM_OK; ++k) {
             rc = lbm_set_launch_shape(ctx, bx, segs[k]);
             if (rc != LBM_OK) break;
-            rc = lbm_step(ctx, 2);
+            // twice the timed count first: captures the graphs the timed
+            // steps replay, from either buffer parity
+            rc = lbm_step(ctx, 2 * (int64_t)steps);
             if (rc == LBM_OK) rc = cuda_fail(ctx, cudaEventRecord(e0, ctx->stream));
             if (rc == LBM_OK) rc = lbm_step(ctx, steps);
             if (rc == LBM_OK) rc = cuda_fail(ctx, cudaEventRecord(e1, ctx->stream));

@@ -66,7 +66,7 @@ def test_batch_matches_oracle_1000_steps():
     b.step(1000)
     b.sync()
     for r, c in zip(b.runs, cases):
-        check_lively(r.fields(), oracle.run_case(c, steps=1000).fields())
+        check_lively(r.fields(), oracle.run_case(c, steps=1000).fields(), oracle, c, 1000)
     b.close()
 
 

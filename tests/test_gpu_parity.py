@@ -18,7 +18,7 @@ from paper_2504_09024_gb300 import lbm, workloads as W
 
 pytestmark = pytest.mark.gpu
 
-from parity import TOL, check_lively, rel, umag
+from parity import TOL, check_lively, rel, umag, vrel
 
 KERNELS = [lbm.LBM_KERNEL_TMA, lbm.LBM_KERNEL_FUSED, lbm.LBM_KERNEL_SPLIT]
 
@@ -43,7 +43,7 @@ def oracle_fields(case, steps):
 def check_fields(got, ref, with_u=True, tol=TOL):
     errs = {k: rel(got[k], ref[k]) for k in ("phi", "c")}
     if with_u:
-        errs["u"] = rel(umag(got), umag(ref))
+        errs["u"] = vrel(got, ref)  # the velocity vector, both components
     for k, e in errs.items():
         assert e <= tol, (k, e, errs)
     return errs
@@ -61,7 +61,7 @@ def test_lively_shear_drop_1000_steps(kernel):
     case = W.lively_shear_drop()
     got = run_gpu(case, kernel, 1000).fields()
     ref = oracle_fields(case, 1000)
-    errs = check_lively(got, ref)
+    errs = check_lively(got, ref, oracle, case, 1000)
     assert rel(got["P"], ref["P"]) < 1e-6, errs
 
 
@@ -86,27 +86,40 @@ def test_periodic_vortex_coupled():
         check_fields(run_gpu(case, kernel).fields(), ref)
 
 
-@pytest.mark.parametrize("shape", [(4, 4), (5, 7), (125, 9), (129, 33), (64, 5)])
+@pytest.mark.parametrize("shape", [(4, 4), (5, 7), (9, 9), (125, 9), (129, 33), (64, 5)])
 @pytest.mark.parametrize("walls", [0, 1])
 def test_small_and_ragged_grids(shape, walls):
+    """Tiny and ragged grids (narrower than the ghost-column width, odd sizes,
+    partial tiles) against the oracle at the 1e-5 bound.  The drop centre sits
+    off the cell centres: on an odd grid a centred drop has |grad phi| = 0 at
+    its middle cell, where the normal jumps between 0 (the oracle's guard)
+    and an arbitrary direction under any perturbation, and with R ~ 2 cells
+    theta is not small there, so 1e-9 of noise changes phi by 5e-4 after one
+    step (measured on the oracle alone)."""
     nx, ny = shape
     phys = W.Physics(nx=nx, ny=ny, walls_y=walls, mode=0, u_wall=0.01 * walls, M_phi=0.05,
                      D_s=0.05, nu_a=0.1, nu_b=0.1, sigma_o=3e-3, beta=0.2)
     R = max(1.5, min(nx, ny) / 3.0)
-    phi, c = W.drop_fields(nx, ny, R, 2.0, c_of_theta=lambda t: 0.2 + 0.1 * np.cos(t))
-    ux, uy = (W.shear_profile(nx, ny, 0.01) if walls else (np.zeros_like(phi), np.zeros_like(phi)))
+    phi, c = W.drop_fields(nx, ny, R, 2.0, xc=nx / 2 + 0.31, yc=ny / 2 + 0.17,
+                           c_of_theta=lambda t: 0.2 + 0.1 * np.cos(t))
+    if walls:
+        ux, uy = W.shear_profile(nx, ny, 0.01)
+    else:
+        # a periodic box gets a uniform stream, so that u is not only the
+        # spurious current of a static drop (a near-zero field whose relative
+        # error measures nothing)
+        ux, uy = np.full_like(phi, 0.01), np.full_like(phi, 0.004)
     case = W.Case(f"small{nx}x{ny}w{walls}", phys, phi, c, ux, uy, None, 60)
     ref = oracle_fields(case, 60)
     for kernel in KERNELS:
         got = run_gpu(case, kernel).fields()
-        # drops of radius 1.5-3 cells are ill-conditioned for FP32 (curvature ~ 1/R
-        # on a 2-cell interface); an indexing or boundary slip gives O(1) errors,
-        # so these grids are held to 1e-4 (the 1e-5 bound applies to the workloads)
-        check_fields(got, ref, tol=1e-4)
+        errs = check_fields(got, ref)
         umax = np.abs(umag(ref)).max()
+        # pointwise: every cell within 1e-4 of the field's largest magnitude
+        # (an indexing or boundary slip gives O(1) errors somewhere)
         for k in ("phi", "c", "ux", "uy", "P"):
             scale = umax if k in ("ux", "uy") else max(np.abs(ref[k]).max(), 1e-12)
-            assert np.abs(got[k] - ref[k]).max() <= 1e-4 * scale + 1e-9, (kernel, k)
+            assert np.abs(got[k] - ref[k]).max() <= 1e-4 * scale, (kernel, k, errs)
 
 
 def test_init_populations_match_oracle():
@@ -174,10 +187,16 @@ def test_bounded_wait_failure_reported():
 
 
 def test_one_step_full_size_2048x1024():
-    """Bench workload size: advance the GPU, hand its state to the oracle,
-    take one more step on both and compare every cell."""
+    """Bench workload size and launch configuration (the TMA sweep at the
+    launch shape the autotuner picks, as the bench runs it): advance the GPU,
+    hand its state to the oracle, take one more step on both and compare
+    every cell."""
     case = W.shear_drop_2048x1024(Ca=0.1, steps=40)
-    s = run_gpu(case, lbm.LBM_KERNEL_FUSED)
+    s = lbm.Sim(case.phys, kernel=lbm.LBM_KERNEL_TMA)
+    s.init(case.phi, case.c, case.ux, case.uy, case.P)
+    s.autotune()
+    s.step(case.steps)
+    assert s.kernel == lbm.LBM_KERNEL_TMA
     pre = s.pops()
     orc = oracle.Sim(case.phys)
     orc.set_pops(**pre)
@@ -417,6 +436,5 @@ def test_density_and_viscosity_ratio_two():
     o.init(case.phi, case.c, case.ux, case.uy)
     o.step(500)
     g, r = s.fields(), o.fields()
-    errs = {"phi": rel(g["phi"], r["phi"]), "c": rel(g["c"], r["c"]), "u": rel(umag(g), umag(r))}
+    errs = check_lively(g, r, oracle, dataclasses.replace(case, phys=phys), 500)
     print("ratio 2:", errs)
-    check_lively(g, r)
