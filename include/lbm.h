@@ -202,6 +202,26 @@ int lbm_launches_per_step(const lbm_ctx *ctx);
 int lbm_set_launch_shape(lbm_ctx *ctx, int32_t tile_x, int32_t seg_y);
 int lbm_get_launch_shape(const lbm_ctx *ctx, int32_t *tile_x, int32_t *seg_y);
 
+/* Cells per thread of the TMA sweep: 1, or 2 horizontally adjacent cells
+ * whose arithmetic runs on the packed two-lane FP32 instructions (tile_x 128
+ * or 192).  Both forms compute the same expressions per cell; they differ
+ * only in where the compiler fuses a multiply and an add (rounding).
+ * Errors: INVALID_ARG (not 1 or 2), UNSUPPORTED (other kernels, or a block
+ * width without the two-cell form). */
+int lbm_set_cells_per_thread(lbm_ctx *ctx, int32_t cells);
+int32_t lbm_get_cells_per_thread(const lbm_ctx *ctx);
+
+/* How the TMA sweep writes collided cells: LBM_STORE_DIRECT (each thread
+ * stores its cells; four staged raw rows in flight) or LBM_STORE_STAGED (each
+ * warp group stages its row in shared memory and one bulk-tensor store writes
+ * it; fewer raw rows in flight).  Same results either way.  FP32 storage
+ * takes both (default DIRECT), 16-bit storage STAGED only.
+ * Errors: INVALID_ARG, UNSUPPORTED. */
+#define LBM_STORE_DIRECT 0
+#define LBM_STORE_STAGED 1
+int lbm_set_store_mode(lbm_ctx *ctx, int32_t mode);
+int32_t lbm_get_store_mode(const lbm_ctx *ctx);
+
 /* Checkpoint: parameters, step count and raw population buffers to a binary
  * file, and back (the file must come from a context with equal parameters).
  * A run continued from a checkpoint is bit-identical to an uninterrupted one.
@@ -235,16 +255,23 @@ int lbm_autotune(lbm_ctx *ctx, int32_t steps, int32_t *tile_x, int32_t *seg_y,
 
 /* ------------------------------------------------------------------------
  * Batches (ensembles of independent runs, e.g. drops in shear at different
- * grid sizes and parameters).  A batch owns one context per run.  Step
- * loops are replayed from captured CUDA graphs of 32 steps that hold one
- * chain of TMA sweep launches per run, the chains spread over up to 16 side
- * streams and run concurrently; a remainder of fewer than 32 steps advances
- * all runs by one persistent launch of the same sweep that walks a list of
- * tiles over all runs (larger runs first).  Runs are independent:
- * each follows Sec. 3 and App. C-D exactly as a single context does, and a
- * batched step gives results identical to stepping each run's context on its
- * own with the same launch shape.
+ * grid sizes and parameters).  A batch owns one context per run and steps
+ * them in one of two forms:
+ *   LBM_BATCH_PERSISTENT  every time step is one launch of a persistent TMA
+ *       sweep over the tiles of all runs (larger runs first), one launch per
+ *       64 runs; all runs share block width, cells per thread and rows per
+ *       tile;
+ *   LBM_BATCH_CHAINS      every run is stepped by its own single-run
+ *       launches with its own launch shape, the runs' launch chains spread
+ *       over up to 16 side streams and running concurrently.
+ * Step loops of either form are replayed from captured CUDA graphs of 32, 16,
+ * 8, 4, 2 and 1 steps.  Runs are independent: each follows Sec. 3 and
+ * App. C-D exactly as a single context does, and a batched step gives
+ * results identical to stepping each run's context on its own with the same
+ * launch shape.
  */
+#define LBM_BATCH_CHAINS 0
+#define LBM_BATCH_PERSISTENT 1
 typedef struct lbm_batch lbm_batch;
 
 /* params: array of nruns parameter sets (grid, physics, walls may differ;
@@ -269,19 +296,33 @@ int lbm_batch_step(lbm_batch *b, int64_t nsteps);
  * bounded wait (LBM_ERR_TIMEOUT) of a batched step. */
 int lbm_batch_synchronize(lbm_batch *b);
 
-/* Block width (64, 128 or 192; the block owns tile_x - 4 columns) and
- * rows per tile (>= 4) of the batched kernel; 0 keeps the current value.
- * The getter also reports the persistent grid size and the number of tiles.
- * Errors: INVALID_ARG, UNSUPPORTED. */
+/* Form of the batched step (LBM_BATCH_PERSISTENT, the default, or
+ * LBM_BATCH_CHAINS).  Synchronous.  Errors: INVALID_ARG. */
+int lbm_batch_set_form(lbm_batch *b, int32_t form);
+int32_t lbm_batch_get_form(const lbm_batch *b);
+
+/* Block width (64, 128 or 192; the block owns tile_x - 4 columns), rows per
+ * tile (>= 4), cells per thread (1 or 2, see lbm_set_cells_per_thread) and
+ * store mode (see lbm_set_store_mode) of the persistent form; 0 keeps the
+ * current width and rows.  Setting them also sets
+ * every run's own shape (chains form).  The getter also reports the
+ * persistent grid size (blocks of all launches of a step) and the number of
+ * tiles.  Errors: INVALID_ARG, UNSUPPORTED. */
 int lbm_batch_set_launch_shape(lbm_batch *b, int32_t tile_x, int32_t seg_y);
+int lbm_batch_set_cells_per_thread(lbm_batch *b, int32_t cells);
+int lbm_batch_set_store_mode(lbm_batch *b, int32_t mode);
 int lbm_batch_get_launch_shape(const lbm_batch *b, int32_t *tile_x, int32_t *seg_y,
                                int32_t *blocks, int32_t *tiles);
 
-/* Autotuner of the batched launch shape: tile_x in {128, 192, 64} x seg_y in
- * {16, 24, 32, 48, 64, 96, 128}, timed and restored as in lbm_autotune
- * (one snapshot buffer per run while it runs).  Each shape is timed on
- * `steps` rounded up to whole 32-step graphs, after one graph of warm-up.
- * Synchronous. */
+/* Autotuner of the batched step: the persistent form over (tile_x, cells
+ * per thread) in {(128, 1), (192, 1), (64, 1), (128, 2), (192, 2)} x both
+ * store modes x seg_y in {16, 32, 48, 64}, and the chains form with every run's shape from
+ * lbm_autotune on one run of each grid size; the fastest form and shape are
+ * kept.  Every candidate is timed over `steps` rounded up to whole 32-step
+ * graphs after one graph of warm-up, and the state, step counts and buffer
+ * parities are restored after each (one snapshot buffer per run while it
+ * runs).  Outputs (nullable): the persistent shape and the chosen form's time
+ * per step in milliseconds.  Synchronous. */
 int lbm_batch_autotune(lbm_batch *b, int32_t steps, int32_t *tile_x, int32_t *seg_y,
                        double *ms_per_step);
 

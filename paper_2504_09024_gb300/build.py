@@ -18,8 +18,8 @@ LIBDIR = os.path.join(HERE, "_lib")
 SO = os.path.join(LIBDIR, "liblbm.so")
 SOURCES = ["lbm_kernels.cu", "lbm_sweep_tma.cu", "lbm_sweep_tma16.cu", "lbm_api.cu", "lbm_noalloc.cu",
            "surr_mlp.cu"]
-HEADERS = ["lbm_device.cuh", "lbm_internal.h", "lbm_cell.cuh", "lbm_tma.cuh", "lbm_sweep_tile.cuh",
-           "lbm_store16.cuh"]
+HEADERS = ["lbm_device.cuh", "lbm_internal.h", "lbm_cell.cuh", "lbm_tma.cuh", "lbm_sweep2.cuh",
+           "lbm_store16.cuh", "lbm_vec.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I" + os.path.join(ROOT, "include")]

@@ -47,12 +47,13 @@ struct lbm_ctx {
     double* dresult = nullptr;
     int diag_nb = 0;
     cudaGraphExec_t graph[GRAPH_CHUNKS][2] = {};  // [log2(32 / steps)][parity]
-    CUtensorMap tmaps[2];   // bulk-tensor maps over the two population buffers
+    CUtensorMap tmaps[2];   // bulk-tensor load maps over the two population buffers
+    lbm::StoreMaps smaps[2];  // bulk-tensor store maps over the same buffers
     // 16-bit storage: the state lives in pop16 (word planes, lbm_store16.cuh);
     // the FP32 buffers stage initialisation and field output
     int st = lbm::ST_F32;
     float* pop16_alloc[2] = {nullptr, nullptr};
-    unsigned* dstep = nullptr;  // step counter of the stochastic rounding (16-bit)
+    unsigned* dstep = nullptr;  // step counter of the stochastic roundings
     int* derr = nullptr;    // device flag: a bounded wait expired
     int pending_error = LBM_OK;
 };
@@ -188,21 +189,21 @@ lbm::KParams make_kparams(const lbm_params& p) {
     return k;
 }
 
+// One time step from buffer src; step_off is the launch's offset within a
+// captured graph (the step counter of the stochastic roundings).
 void launch_one_step(lbm_ctx* ctx, int src, cudaStream_t st, int step_off = 0) {
-    if (ctx->st != lbm::ST_F32) {
-        lbm::KParams kp = ctx->kp;
-        kp.step_off = step_off;
-        lbm::launch_step_tma16(kp, ctx->pop16_alloc[src] + lbm::XGHOST,
-                               ctx->pop16_alloc[1 - src] + lbm::XGHOST, ctx->ds.fields, ctx->shape,
-                               ctx->tmaps[src], ctx->st, ctx->derr, st);
-        return;
+    lbm::KParams kp = ctx->kp;
+    kp.step_off = step_off;
+    if (ctx->kernel == LBM_KERNEL_TMA) {
+        float* dst = ctx->st == lbm::ST_F32 ? ctx->ds.pop[1 - src]
+                                            : ctx->pop16_alloc[1 - src] + lbm::XGHOST;
+        lbm::launch_step_sweep2(kp, dst, ctx->ds.fields, ctx->shape, ctx->tmaps[src],
+                                ctx->smaps[1 - src], ctx->st, ctx->derr, st);
+    } else if (ctx->kernel == LBM_KERNEL_SPLIT) {
+        lbm::launch_step_split(kp, ctx->ds, src, st);
+    } else {
+        lbm::launch_step_fused(kp, ctx->ds, src, ctx->shape, st);
     }
-    if (ctx->kernel == LBM_KERNEL_SPLIT)
-        lbm::launch_step_split(ctx->kp, ctx->ds, src, st);
-    else if (ctx->kernel == LBM_KERNEL_TMA)
-        lbm::launch_step_tma(ctx->kp, ctx->ds, src, ctx->shape, ctx->tmaps, ctx->derr, st);
-    else
-        lbm::launch_step_fused(ctx->kp, ctx->ds, src, ctx->shape, st);
 }
 
 int build_tensor_maps(lbm_ctx* ctx) {
@@ -210,10 +211,18 @@ int build_tensor_maps(lbm_ctx* ctx) {
     const int nplanes = lbm::store_planes(ctx->st, ctx->kp.coupled);
     for (int b = 0; b < 2; ++b) {
         float* base = ctx->st == lbm::ST_F32 ? ctx->pop_alloc[b] : ctx->pop16_alloc[b];
-        if (!lbm::make_tensor_map(&ctx->tmaps[b], base, ctx->kp, nplanes, ctx->shape.bx))
+        if (!lbm::make_tensor_map(&ctx->tmaps[b], base, ctx->kp, nplanes, ctx->shape.bx) ||
+            !lbm::make_store_maps(&ctx->smaps[b], base, ctx->kp, ctx->st, ctx->shape.bx))
             return LBM_ERR_UNSUPPORTED;
     }
     return LBM_OK;
+}
+
+// Launch shape of a single run (the caller has checked it).
+int set_shape(lbm_ctx* ctx, const lbm::FusedShape& sh) {
+    ctx->shape = sh;
+    drop_graphs(ctx);
+    return build_tensor_maps(ctx);
 }
 
 // The device step counter of the stochastic rounding follows ctx->step
@@ -322,6 +331,8 @@ int lbm_create(const lbm_params* p, void* stream, lbm_ctx** out) {
                                                                        : LBM_KERNEL_FUSED)
                                                : p->kernel;
     ctx->st = p->dtype == LBM_F16S ? lbm::ST_F16 : (p->dtype == LBM_BF16S ? lbm::ST_BF16 : lbm::ST_F32);
+    // 16-bit rows leave through the staging area (staged bulk-tensor stores)
+    ctx->shape.out = ctx->st == lbm::ST_F32 ? lbm::OUT_DIRECT : lbm::OUT_STAGED;
     if (ctx->kernel == LBM_KERNEL_TMA && !lbm::tma_available()) {
         delete ctx;
         return LBM_ERR_UNSUPPORTED;
@@ -340,8 +351,7 @@ int lbm_create(const lbm_params* p, void* stream, lbm_ctx** out) {
         lbm_destroy(ctx);
         return LBM_ERR_CUDA;
     }
-    if (lbm::configure_fused_smem() != cudaSuccess || lbm::configure_tma_smem() != cudaSuccess ||
-        lbm::configure_tma16_smem() != cudaSuccess) {
+    if (lbm::configure_fused_smem() != cudaSuccess || lbm::configure_sweep2_smem() != cudaSuccess) {
         cudaGetLastError();
         lbm_destroy(ctx);
         return LBM_ERR_CUDA;
@@ -356,9 +366,9 @@ int lbm_create(const lbm_params* p, void* stream, lbm_ctx** out) {
         cudaMalloc(&ctx->dpartial, sizeof(double) * lbm::DIAG_NSUM * ctx->diag_nb) != cudaSuccess ||
         cudaMalloc(&ctx->dresult, sizeof(double) * 16) != cudaSuccess ||
         cudaMalloc(&ctx->derr, sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&ctx->dstep, sizeof(unsigned)) != cudaSuccess ||
         (ctx->st != lbm::ST_F32 &&
-         (cudaMalloc(&ctx->dstep, sizeof(unsigned)) != cudaSuccess ||
-          cudaMalloc(&ctx->pop16_alloc[0], sizeof(float) * state_words(ctx)) != cudaSuccess ||
+         (cudaMalloc(&ctx->pop16_alloc[0], sizeof(float) * state_words(ctx)) != cudaSuccess ||
           cudaMalloc(&ctx->pop16_alloc[1], sizeof(float) * state_words(ctx)) != cudaSuccess))) {
         cudaGetLastError();
         lbm_destroy(ctx);
@@ -624,9 +634,10 @@ int lbm_synchronize(lbm_ctx* ctx) {
     e = cudaMemcpy(&timed_out, ctx->derr, sizeof(int), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(ctx, e);
     if (timed_out) {
+        // 1: a bounded wait expired; 2: a kernel found its shared memory misaligned
         cudaMemset(ctx->derr, 0, sizeof(int));
         ctx->pending_error = LBM_OK;
-        return LBM_ERR_TIMEOUT;
+        return timed_out == 1 ? LBM_ERR_TIMEOUT : LBM_ERR_CUDA;
     }
     int pend = ctx->pending_error;
     ctx->pending_error = LBM_OK;
@@ -649,8 +660,8 @@ int lbm_set_launch_shape(lbm_ctx* ctx, int32_t tile_x, int32_t seg_y) {
         return LBM_ERR_INVALID_ARG;
     if (seg_y != 0 && seg_y < 4) return LBM_ERR_INVALID_ARG;
     const bool tma = ctx->kernel == LBM_KERNEL_TMA;
-    const bool ok_bx = tile_x == 0 || tile_x == 128 || (tile_x == 192 && tma) ||
-                       (tile_x == 64 && tma && ctx->st == lbm::ST_F32);
+    const bool ok_bx = tile_x == 0 || (tma ? lbm::sweep2_shape_ok(tile_x, ctx->shape.cpt, ctx->st)
+                                           : tile_x == 128);
     if (!ok_bx) return LBM_ERR_UNSUPPORTED;
     if (tile_x) ctx->shape.bx = tile_x;
     if (seg_y) ctx->shape.seg = seg_y;
@@ -663,6 +674,32 @@ int lbm_get_launch_shape(const lbm_ctx* ctx, int32_t* tile_x, int32_t* seg_y) {
     if (tile_x) *tile_x = ctx->shape.bx;
     if (seg_y) *seg_y = ctx->shape.seg;
     return LBM_OK;
+}
+
+int lbm_set_cells_per_thread(lbm_ctx* ctx, int32_t cells) {
+    if (!ctx || cells < 1 || cells > 2) return LBM_ERR_INVALID_ARG;
+    if (ctx->kernel != LBM_KERNEL_TMA) return cells == 1 ? LBM_OK : LBM_ERR_UNSUPPORTED;
+    if (!lbm::sweep2_shape_ok(ctx->shape.bx, cells, ctx->st)) return LBM_ERR_UNSUPPORTED;
+    ctx->shape.cpt = cells;
+    drop_graphs(ctx);
+    return LBM_OK;
+}
+
+int32_t lbm_get_cells_per_thread(const lbm_ctx* ctx) {
+    return ctx ? ctx->shape.cpt : LBM_ERR_INVALID_ARG;
+}
+
+int lbm_set_store_mode(lbm_ctx* ctx, int32_t mode) {
+    if (!ctx || (mode != LBM_STORE_DIRECT && mode != LBM_STORE_STAGED)) return LBM_ERR_INVALID_ARG;
+    if (ctx->kernel != LBM_KERNEL_TMA) return mode == LBM_STORE_DIRECT ? LBM_OK : LBM_ERR_UNSUPPORTED;
+    if (mode == LBM_STORE_DIRECT && ctx->st != lbm::ST_F32) return LBM_ERR_UNSUPPORTED;
+    ctx->shape.out = mode;
+    drop_graphs(ctx);
+    return LBM_OK;
+}
+
+int32_t lbm_get_store_mode(const lbm_ctx* ctx) {
+    return ctx ? ctx->shape.out : LBM_ERR_INVALID_ARG;
 }
 
 // Checkpoint file: magic, ABI version, parameters, step, buffer sizes, then
@@ -759,12 +796,15 @@ int lbm_load_state(lbm_ctx* ctx, const char* path) {
 }  // extern "C"
 
 // ---------------------------------------------------------------------------
-// Batches: many runs advanced together.  Captured graphs of GRAPH_STEPS steps
-// hold one chain of single-run launches per run, spread over side streams
-// (the chains are independent, so the graph runs them concurrently and each
-// launch keeps its run's parameters in the constant bank); steps outside a
-// graph (and the failure-path test hook) use one persistent launch over the
-// tiles of all runs.  Both kernels run the same per-cell arithmetic.
+// Batches: many runs advanced together, in one of two forms.
+//  * persistent: every step is one launch of the persistent batch kernel over
+//    the tiles of all runs (one launch per table of BATCH_TABLE_RUNS runs);
+//    all runs share the block width, cells per thread and rows per tile.
+//  * chains: every run is stepped by its own single-run launches, each run
+//    with its own launch shape, the runs' chains spread over side streams.
+// Either form is replayed from captured graphs of 32, 16, 8, 4, 2 and 1
+// steps.  Both run the same tile sweep, so a batched step gives the same bits
+// as stepping each run's context on its own with the same launch shape.
 // ---------------------------------------------------------------------------
 
 struct lbm_batch {
@@ -774,18 +814,25 @@ struct lbm_batch {
     bool own_stream = false;
     cudaStream_t cap_stream = nullptr;
     bool coupled = true;
-    lbm::FusedShape shape{128, 32};
-    int blocks = 0;                 // persistent grid size
-    int nitems = 0;                 // tiles over all runs
-    lbm::RunDesc* hdesc = nullptr;  // host copy of the run table
+    int form = LBM_BATCH_PERSISTENT;
+    lbm::FusedShape shape{192, 32, 1};  // shape of the persistent form
+    // persistent form: tables of run parameters, tile lists, grids
+    int ntab = 0;
+    lbm::BatchTable* htab = nullptr;    // [ntab]
+    int* tab_off = nullptr;             // [ntab + 1] tile-list offsets
+    int* tab_blocks = nullptr;          // [ntab] grid sizes
+    int nitems = 0;
+    lbm::RunDesc* hdesc = nullptr;      // host copy of the run table
     lbm::RunDesc* ddesc = nullptr;
     int4* ditems = nullptr;
+    unsigned** dctrs = nullptr;         // the runs' step counters (device array)
+    lbm::KParams* hkp = nullptr;        // the runs' parameters the graphs were built with
     int* derr = nullptr;
     int parity = 0;
     bool desc_valid = false;
-    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    cudaGraphExec_t graph[GRAPH_CHUNKS][2] = {};
     int pending_error = LBM_OK;
-    // graph capture: side streams for the per-run chains, fork/join events
+    // chains form: side streams for the per-run chains, fork/join events
     int nside = 0;
     cudaStream_t side[BATCH_SIDE_STREAMS] = {};
     cudaEvent_t fork_ev = nullptr;
@@ -795,11 +842,12 @@ struct lbm_batch {
 namespace {
 
 void batch_drop_graphs(lbm_batch* b) {
-    for (int k = 0; k < 2; ++k)
-        if (b->graph[k]) {
-            cudaGraphExecDestroy(b->graph[k]);
-            b->graph[k] = nullptr;
-        }
+    for (int c = 0; c < GRAPH_CHUNKS; ++c)
+        for (int k = 0; k < 2; ++k)
+            if (b->graph[c][k]) {
+                cudaGraphExecDestroy(b->graph[c][k]);
+                b->graph[c][k] = nullptr;
+            }
 }
 
 int batch_fail(lbm_batch* b, cudaError_t e) {
@@ -809,7 +857,8 @@ int batch_fail(lbm_batch* b, cudaError_t e) {
     return LBM_ERR_CUDA;
 }
 
-// Tensor maps, tile list and persistent grid for the current launch shape.
+// Tensor maps, parameter tables, tile lists and grids of the persistent form
+// for its current launch shape; run tables to the device.
 int batch_build_tiles(lbm_batch* b) {
     batch_drop_graphs(b);
     const int bx = b->shape.bx, tx = bx - 4;
@@ -821,51 +870,65 @@ int batch_build_tiles(lbm_batch* b) {
     }
     if (total > (int64_t)1 << 30) return LBM_ERR_INVALID_ARG;
     int4* items = (int4*)std::malloc(sizeof(int4) * (size_t)total);
-    if (!items) return LBM_ERR_NOMEM;
-    // larger runs first: the tail of the persistent loop is made of small tiles
     int* order = (int*)std::malloc(sizeof(int) * (size_t)b->nruns);
-    if (!order) {
+    if (!items || !order) {
         std::free(items);
+        std::free(order);
         return LBM_ERR_NOMEM;
     }
-    for (int r = 0; r < b->nruns; ++r) order[r] = r;
-    for (int a = 1; a < b->nruns; ++a) {  // insertion sort by cell count, stable
-        const int v = order[a];
-        const int64_t cv = (int64_t)b->runs[v]->kp.nx * b->runs[v]->kp.ny;
-        int k = a - 1;
-        while (k >= 0 && (int64_t)b->runs[order[k]]->kp.nx * b->runs[order[k]]->kp.ny < cv) {
-            order[k + 1] = order[k];
-            --k;
-        }
-        order[k + 1] = v;
-    }
+    const int per_sm = lbm::sweep2_batch_blocks_per_sm(bx, b->shape.cpt, b->shape.out, b->coupled);
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     int64_t n = 0;
-    for (int a = 0; a < b->nruns; ++a) {
-        const int r = order[a];
-        const lbm_ctx* c = b->runs[r];
-        const int nsx = (c->kp.nx + tx - 1) / tx, nsy = (c->kp.ny + b->shape.seg - 1) / b->shape.seg;
-        for (int sy = 0; sy < nsy; ++sy)
-            for (int sx = 0; sx < nsx; ++sx) items[n++] = make_int4(r, sx, sy, 0);
+    for (int t = 0; t < b->ntab; ++t) {
+        const int r0 = t * lbm::BATCH_TABLE_RUNS;
+        const int r1 = std::min(b->nruns, r0 + lbm::BATCH_TABLE_RUNS);
+        // larger runs first: the tail of the persistent loop is made of small tiles
+        int m = 0;
+        for (int r = r0; r < r1; ++r) {
+            const int64_t cv = (int64_t)b->runs[r]->kp.nx * b->runs[r]->kp.ny;
+            int k = m - 1;
+            while (k >= 0 && (int64_t)b->runs[order[k]]->kp.nx * b->runs[order[k]]->kp.ny < cv) {
+                order[k + 1] = order[k];
+                --k;
+            }
+            order[k + 1] = r;
+            ++m;
+        }
+        b->tab_off[t] = (int)n;
+        for (int a = 0; a < m; ++a) {
+            const int r = order[a];
+            const lbm_ctx* c = b->runs[r];
+            const int nsx = (c->kp.nx + tx - 1) / tx, nsy = (c->kp.ny + b->shape.seg - 1) / b->shape.seg;
+            for (int sy = 0; sy < nsy; ++sy)
+                for (int sx = 0; sx < nsx; ++sx) items[n++] = make_int4(r - r0, sx, sy, r);
+        }
+        const int tiles = (int)(n - b->tab_off[t]);
+        b->tab_blocks[t] = (int)std::min<int64_t>(tiles, (int64_t)per_sm * (nsm > 0 ? nsm : 1));
     }
+    b->tab_off[b->ntab] = (int)n;
     std::free(order);
     for (int r = 0; r < b->nruns; ++r) {
         lbm_ctx* c = b->runs[r];
         lbm::RunDesc& d = b->hdesc[r];
         for (int k = 0; k < 2; ++k) {
-            if (!lbm::make_tensor_map(&d.tmap[k], c->pop_alloc[k], c->kp, nl * 9, bx)) {
+            if (!lbm::make_tensor_map(&d.tmap[k], c->pop_alloc[k], c->kp, nl * 9, bx) ||
+                !lbm::make_store_maps(&d.smap[k], c->pop_alloc[k], c->kp, lbm::ST_F32, bx)) {
                 std::free(items);
                 return LBM_ERR_UNSUPPORTED;
             }
             d.pop[k] = c->ds.pop[k];
         }
-        d.p = c->kp;
         d.fields = c->ds.fields;
         d.seg = b->shape.seg;
         d.flip = c->cur ^ b->parity;
+        b->hkp[r] = c->kp;
+        b->htab[r / lbm::BATCH_TABLE_RUNS].p[r % lbm::BATCH_TABLE_RUNS] = c->kp;
     }
     cudaFree(b->ditems);
     b->ditems = nullptr;
-    cudaError_t e = cudaMalloc(&b->ditems, sizeof(int4) * (size_t)total);
+    cudaError_t e = cudaMalloc(&b->ditems, sizeof(int4) * (size_t)std::max<int64_t>(total, 1));
     if (e == cudaSuccess)
         e = cudaMemcpy(b->ditems, items, sizeof(int4) * (size_t)total, cudaMemcpyHostToDevice);
     std::free(items);
@@ -873,11 +936,6 @@ int batch_build_tiles(lbm_batch* b) {
         e = cudaMemcpy(b->ddesc, b->hdesc, sizeof(lbm::RunDesc) * b->nruns, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return batch_fail(b, e);
     b->nitems = (int)total;
-    int dev = 0, nsm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    const int per_sm = lbm::tma_batch_blocks_per_sm(bx, b->coupled);
-    b->blocks = (int)std::min<int64_t>(total, (int64_t)per_sm * (nsm > 0 ? nsm : 1));
     b->desc_valid = true;
     return LBM_OK;
 }
@@ -890,13 +948,14 @@ int batch_sync_desc(lbm_batch* b) {
     for (int r = 0; r < b->nruns && !dirty; ++r) {
         const lbm_ctx* c = b->runs[r];
         dirty = b->hdesc[r].flip != (c->cur ^ b->parity) ||
-                std::memcmp(&b->hdesc[r].p, &c->kp, sizeof(lbm::KParams)) != 0;
+                std::memcmp(&b->hkp[r], &c->kp, sizeof(lbm::KParams)) != 0;
     }
     if (!dirty) return LBM_OK;
     batch_drop_graphs(b);  // the graphs' launches carry the old parities and parameters
     for (int r = 0; r < b->nruns; ++r) {
         b->hdesc[r].flip = b->runs[r]->cur ^ b->parity;
-        b->hdesc[r].p = b->runs[r]->kp;
+        b->hkp[r] = b->runs[r]->kp;
+        b->htab[r / lbm::BATCH_TABLE_RUNS].p[r % lbm::BATCH_TABLE_RUNS] = b->runs[r]->kp;
     }
     cudaError_t e = cudaMemcpyAsync(b->ddesc, b->hdesc, sizeof(lbm::RunDesc) * b->nruns,
                                     cudaMemcpyHostToDevice, b->stream);
@@ -905,19 +964,27 @@ int batch_sync_desc(lbm_batch* b) {
     return batch_fail(b, e);
 }
 
-void batch_launch(lbm_batch* b, int parity, cudaStream_t st) {
-    lbm::launch_step_tma_batch(b->ddesc, b->ditems, b->nitems, b->blocks, b->shape.bx, b->coupled,
-                               parity, b->derr, st);
+// n steps of the persistent form from batch parity `parity` on stream st
+// (step_off: offset of the first step within its graph).
+void batch_persistent_steps(lbm_batch* b, int parity, int n, cudaStream_t st) {
+    for (int s = 0; s < n; ++s)
+        for (int t = 0; t < b->ntab; ++t) {
+            lbm::BatchTable& tab = b->htab[t];
+            const int r0 = t * lbm::BATCH_TABLE_RUNS;
+            const int r1 = std::min(b->nruns, r0 + lbm::BATCH_TABLE_RUNS);
+            for (int r = r0; r < r1; ++r) tab.p[r - r0].step_off = s;
+            lbm::launch_sweep2_batch(tab, b->ddesc, b->ditems + b->tab_off[t],
+                                     b->tab_off[t + 1] - b->tab_off[t], b->tab_blocks[t],
+                                     b->shape, b->coupled, parity ^ (s & 1), b->derr, st);
+        }
+    lbm::launch_step_advance_many(b->dctrs, b->nruns, (unsigned)n, st);
 }
 
-// One graph of GRAPH_STEPS steps: run r's chain of launches starts from
-// buffer parity ^ flip[r].  Runs go to the side streams largest first, each
-// to the stream with the fewest cells so far, so the chains end together.
-int batch_build_graph(lbm_batch* b, int parity) {
-    cudaGraph_t g = nullptr;
-    cudaError_t e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal);
-    if (e != cudaSuccess) return batch_fail(b, e);
-    e = cudaEventRecord(b->fork_ev, b->cap_stream);
+// n steps of the chains form: run r's chain starts from its buffer
+// parity ^ flip[r].  Runs go to the side streams largest first, each to the
+// stream with the fewest cells so far, so the chains end together.
+cudaError_t batch_chain_steps(lbm_batch* b, int parity, int n, cudaStream_t st) {
+    cudaError_t e = cudaEventRecord(b->fork_ev, st);
     for (int k = 0; k < b->nside && e == cudaSuccess; ++k)
         e = cudaStreamWaitEvent(b->side[k], b->fork_ev, 0);
     int64_t load[BATCH_SIDE_STREAMS] = {};
@@ -927,7 +994,7 @@ int batch_build_graph(lbm_batch* b, int parity) {
         int r = -1;
         int64_t best = -1;
         for (int q = 0; q < b->nruns; ++q) {
-            const int64_t cells = (int64_t)b->hdesc[q].p.nx * b->hdesc[q].p.ny;
+            const int64_t cells = (int64_t)b->runs[q]->kp.nx * b->runs[q]->kp.ny;
             if (!done[q] && cells > best) {
                 best = cells;
                 r = q;
@@ -938,18 +1005,38 @@ int batch_build_graph(lbm_batch* b, int parity) {
         for (int q = 1; q < b->nside; ++q)
             if (load[q] < load[k]) k = q;
         load[k] += best;
-        const lbm::RunDesc& d = b->hdesc[r];
-        int src = parity ^ d.flip;
-        for (int s = 0; s < GRAPH_STEPS; ++s) {
-            lbm::launch_step_tma(d.p, b->runs[r]->ds, src, b->shape, d.tmap, b->derr, b->side[k]);
+        lbm_ctx* c = b->runs[r];
+        int src = parity ^ b->hdesc[r].flip;
+        for (int s = 0; s < n; ++s) {
+            lbm::KParams kp = c->kp;
+            kp.step_off = s;
+            float* dst = c->ds.pop[1 - src];
+            lbm::launch_step_sweep2(kp, dst, c->ds.fields, c->shape, c->tmaps[src],
+                                    c->smaps[1 - src], lbm::ST_F32, b->derr, b->side[k]);
             src ^= 1;
         }
+        lbm::launch_step_advance(c->dstep, (unsigned)n, b->side[k]);
         e = cudaGetLastError();
     }
     std::free(done);
     for (int k = 0; k < b->nside && e == cudaSuccess; ++k) {
         e = cudaEventRecord(b->join_ev[k], b->side[k]);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->cap_stream, b->join_ev[k], 0);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, b->join_ev[k], 0);
+    }
+    return e;
+}
+
+// Graph of GRAPH_STEPS >> chunk steps of the batch's form from batch parity `parity`.
+int batch_build_graph(lbm_batch* b, int parity, int chunk) {
+    const int n = GRAPH_STEPS >> chunk;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return batch_fail(b, e);
+    if (b->form == LBM_BATCH_PERSISTENT) {
+        batch_persistent_steps(b, parity, n, b->cap_stream);
+        e = cudaGetLastError();
+    } else {
+        e = batch_chain_steps(b, parity, n, b->cap_stream);
     }
     const cudaError_t ee = cudaStreamEndCapture(b->cap_stream, &g);
     if (e == cudaSuccess) e = ee;
@@ -957,7 +1044,7 @@ int batch_build_graph(lbm_batch* b, int parity) {
         if (g) cudaGraphDestroy(g);
         return batch_fail(b, e);
     }
-    e = cudaGraphInstantiate(&b->graph[parity], g, 0);
+    e = cudaGraphInstantiate(&b->graph[chunk][parity], g, 0);
     cudaGraphDestroy(g);
     return batch_fail(b, e);
 }
@@ -991,9 +1078,14 @@ int lbm_batch_create(const lbm_params* params, int32_t nruns, void* stream, lbm_
         }
         b->own_stream = true;
     }
+    b->ntab = (nruns + lbm::BATCH_TABLE_RUNS - 1) / lbm::BATCH_TABLE_RUNS;
     b->runs = (lbm_ctx**)std::calloc((size_t)nruns, sizeof(lbm_ctx*));
     b->hdesc = (lbm::RunDesc*)std::calloc((size_t)nruns, sizeof(lbm::RunDesc));
-    if (!b->runs || !b->hdesc) {
+    b->hkp = (lbm::KParams*)std::calloc((size_t)nruns, sizeof(lbm::KParams));
+    b->htab = (lbm::BatchTable*)std::calloc((size_t)b->ntab, sizeof(lbm::BatchTable));
+    b->tab_off = (int*)std::calloc((size_t)b->ntab + 1, sizeof(int));
+    b->tab_blocks = (int*)std::calloc((size_t)b->ntab, sizeof(int));
+    if (!b->runs || !b->hdesc || !b->hkp || !b->htab || !b->tab_off || !b->tab_blocks) {
         lbm_batch_destroy(b);
         return LBM_ERR_NOMEM;
     }
@@ -1020,13 +1112,32 @@ int lbm_batch_create(const lbm_params* params, int32_t nruns, void* stream, lbm_
         }
         b->nruns = r + 1;
     }
-    if (cudaMalloc(&b->ddesc, sizeof(lbm::RunDesc) * (size_t)nruns) != cudaSuccess ||
-        cudaMalloc(&b->derr, sizeof(int)) != cudaSuccess) {
+    unsigned** hctrs = (unsigned**)std::malloc(sizeof(unsigned*) * (size_t)nruns);
+    if (!hctrs) {
+        lbm_batch_destroy(b);
+        return LBM_ERR_NOMEM;
+    }
+    for (int r = 0; r < nruns; ++r) hctrs[r] = b->runs[r]->dstep;
+    cudaError_t e = cudaMalloc(&b->ddesc, sizeof(lbm::RunDesc) * (size_t)nruns);
+    if (e == cudaSuccess) e = cudaMalloc(&b->derr, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&b->dctrs, sizeof(unsigned*) * (size_t)nruns);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(b->dctrs, hctrs, sizeof(unsigned*) * (size_t)nruns, cudaMemcpyHostToDevice);
+    std::free(hctrs);
+    if (e != cudaSuccess) {
         cudaGetLastError();
         lbm_batch_destroy(b);
         return LBM_ERR_NOMEM;
     }
     cudaMemset(b->derr, 0, sizeof(int));
+    // the runs' own shapes (chains form) follow the persistent shape until tuned
+    for (int r = 0; r < nruns; ++r) {
+        const int rc = set_shape(b->runs[r], b->shape);
+        if (rc != LBM_OK) {
+            lbm_batch_destroy(b);
+            return rc;
+        }
+    }
     const int rc = batch_build_tiles(b);
     if (rc != LBM_OK) {
         lbm_batch_destroy(b);
@@ -1043,8 +1154,13 @@ void lbm_batch_destroy(lbm_batch* b) {
     for (int r = 0; r < b->nruns; ++r) lbm_destroy(b->runs[r]);
     std::free(b->runs);
     std::free(b->hdesc);
+    std::free(b->hkp);
+    std::free(b->htab);
+    std::free(b->tab_off);
+    std::free(b->tab_blocks);
     cudaFree(b->ddesc);
     cudaFree(b->ditems);
+    cudaFree(b->dctrs);
     cudaFree(b->derr);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
     for (int k = 0; k < BATCH_SIDE_STREAMS; ++k) {
@@ -1071,37 +1187,41 @@ int lbm_batch_step(lbm_batch* b, int64_t nsteps) {
     for (int r = 0; r < b->nruns; ++r) stall = stall || b->runs[r]->kp.stall_test;
     int64_t left = nsteps;
     while (left > 0) {
-        if (left >= GRAPH_STEPS && !stall) {
-            if (!b->graph[b->parity]) {
-                rc = batch_build_graph(b, b->parity);
-                if (rc != LBM_OK) return rc;
-            }
-            if (cudaGraphLaunch(b->graph[b->parity], b->stream) != cudaSuccess)
-                return batch_fail(b, cudaGetLastError());
-            left -= GRAPH_STEPS;  // even: parity unchanged
-        } else {
-            batch_launch(b, b->parity, b->stream);
+        if (stall) {
+            // the test hook: one uncaptured step with the stall flags, then clear them
+            const cudaError_t e = b->form == LBM_BATCH_PERSISTENT
+                                      ? (batch_persistent_steps(b, b->parity, 1, b->stream),
+                                         cudaGetLastError())
+                                      : batch_chain_steps(b, b->parity, 1, b->stream);
+            if (e != cudaSuccess) return batch_fail(b, e);
             b->parity ^= 1;
             left -= 1;
-            if (stall) {  // the hook stalls one step only
-                for (int r = 0; r < b->nruns; ++r) b->hdesc[r].p.stall_test = 0;
-                cudaError_t e = cudaMemcpyAsync(b->ddesc, b->hdesc, sizeof(lbm::RunDesc) * b->nruns,
-                                                cudaMemcpyHostToDevice, b->stream);
-                if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
-                if (e != cudaSuccess) return batch_fail(b, e);
-                stall = false;
+            for (int r = 0; r < b->nruns; ++r) {
+                b->runs[r]->kp.stall_test = 0;
+                b->hkp[r].stall_test = 0;
+                b->htab[r / lbm::BATCH_TABLE_RUNS].p[r % lbm::BATCH_TABLE_RUNS].stall_test = 0;
+                drop_graphs(b->runs[r]);
             }
+            stall = false;
+            continue;
         }
+        int chunk = 0;
+        while ((GRAPH_STEPS >> chunk) > left) ++chunk;
+        const int n = GRAPH_STEPS >> chunk;
+        if (!b->graph[chunk][b->parity]) {
+            rc = batch_build_graph(b, b->parity, chunk);
+            if (rc != LBM_OK) return rc;
+        }
+        if (cudaGraphLaunch(b->graph[chunk][b->parity], b->stream) != cudaSuccess)
+            return batch_fail(b, cudaGetLastError());
+        b->parity ^= n & 1;
+        left -= n;
     }
     // every run advanced by nsteps: its current buffer follows the batch parity
     for (int r = 0; r < b->nruns; ++r) {
         lbm_ctx* c = b->runs[r];
         c->cur = b->parity ^ b->hdesc[r].flip;
         c->step += nsteps;
-        if (c->kp.stall_test && nsteps > 0) {  // the one-shot test hook was taken by this call
-            c->kp.stall_test = 0;
-            drop_graphs(c);
-        }
     }
     return batch_fail(b, cudaGetLastError());
 }
@@ -1116,21 +1236,63 @@ int lbm_batch_synchronize(lbm_batch* b) {
     if (timed_out) {
         cudaMemset(b->derr, 0, sizeof(int));
         b->pending_error = LBM_OK;
-        return LBM_ERR_TIMEOUT;
+        return timed_out == 1 ? LBM_ERR_TIMEOUT : LBM_ERR_CUDA;
     }
     const int pend = b->pending_error;
     b->pending_error = LBM_OK;
     return pend;
 }
 
+int lbm_batch_set_form(lbm_batch* b, int32_t form) {
+    if (!b || (form != LBM_BATCH_CHAINS && form != LBM_BATCH_PERSISTENT))
+        return LBM_ERR_INVALID_ARG;
+    const int rc = lbm_batch_synchronize(b);
+    if (rc != LBM_OK) return rc;
+    b->form = form;
+    batch_drop_graphs(b);
+    return LBM_OK;
+}
+
+int32_t lbm_batch_get_form(const lbm_batch* b) { return b ? b->form : LBM_ERR_INVALID_ARG; }
+
 int lbm_batch_set_launch_shape(lbm_batch* b, int32_t tile_x, int32_t seg_y) {
     if (!b) return LBM_ERR_INVALID_ARG;
-    if (tile_x != 0 && tile_x != 64 && tile_x != 128 && tile_x != 192) return LBM_ERR_UNSUPPORTED;
+    if (tile_x != 0 && !lbm::sweep2_shape_ok(tile_x, b->shape.cpt, lbm::ST_F32))
+        return LBM_ERR_UNSUPPORTED;
     if (seg_y != 0 && seg_y < 4) return LBM_ERR_INVALID_ARG;
     const int rc = lbm_batch_synchronize(b);
     if (rc != LBM_OK) return rc;
     if (tile_x) b->shape.bx = tile_x;
     if (seg_y) b->shape.seg = seg_y;
+    for (int r = 0; r < b->nruns; ++r) {
+        const int rr = set_shape(b->runs[r], b->shape);
+        if (rr != LBM_OK) return rr;
+    }
+    return batch_build_tiles(b);
+}
+
+int lbm_batch_set_store_mode(lbm_batch* b, int32_t mode) {
+    if (!b || (mode != LBM_STORE_DIRECT && mode != LBM_STORE_STAGED)) return LBM_ERR_INVALID_ARG;
+    const int rc = lbm_batch_synchronize(b);
+    if (rc != LBM_OK) return rc;
+    b->shape.out = mode;
+    for (int r = 0; r < b->nruns; ++r) {
+        const int rr = set_shape(b->runs[r], b->shape);
+        if (rr != LBM_OK) return rr;
+    }
+    return batch_build_tiles(b);
+}
+
+int lbm_batch_set_cells_per_thread(lbm_batch* b, int32_t cells) {
+    if (!b || cells < 1 || cells > 2) return LBM_ERR_INVALID_ARG;
+    if (!lbm::sweep2_shape_ok(b->shape.bx, cells, lbm::ST_F32)) return LBM_ERR_UNSUPPORTED;
+    const int rc = lbm_batch_synchronize(b);
+    if (rc != LBM_OK) return rc;
+    b->shape.cpt = cells;
+    for (int r = 0; r < b->nruns; ++r) {
+        const int rr = set_shape(b->runs[r], b->shape);
+        if (rr != LBM_OK) return rr;
+    }
     return batch_build_tiles(b);
 }
 
@@ -1139,7 +1301,9 @@ int lbm_batch_get_launch_shape(const lbm_batch* b, int32_t* tile_x, int32_t* seg
     if (!b) return LBM_ERR_INVALID_ARG;
     if (tile_x) *tile_x = b->shape.bx;
     if (seg_y) *seg_y = b->shape.seg;
-    if (blocks) *blocks = b->blocks;
+    int nb = 0;
+    for (int t = 0; t < b->ntab; ++t) nb += b->tab_blocks[t];
+    if (blocks) *blocks = nb;
     if (tiles) *tiles = b->nitems;
     return LBM_OK;
 }
@@ -1207,17 +1371,31 @@ int lbm_autotune(lbm_ctx* ctx, int32_t steps, int32_t* tile_x, int32_t* seg_y,
     if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
     double best = 1e300;
     lbm::FusedShape best_shape = shape0;
-    const int bxs[3] = {128, 192, 64};
-    const int nbx = ctx->kernel != LBM_KERNEL_TMA ? 1 : ctx->st == lbm::ST_F32 ? 3 : 2;
-    for (int a = 0; a < nbx && ce == cudaSuccess && rc == LBM_OK; ++a) {
-        const int bx = bxs[a];
-        const int per_sm = ctx->kernel != LBM_KERNEL_TMA ? 2
-                           : ctx->st != lbm::ST_F32   ? lbm::tma16_blocks_per_sm(bx, ctx->kp.coupled, ctx->st)
-                                                      : lbm::tma_blocks_per_sm(bx, ctx->kp.coupled);
+    // (block width, cells per thread, store mode) candidates of the kernel in use
+    int cand[10][3] = {{128, 1, 0}};
+    int ncand = 1;
+    if (ctx->kernel == LBM_KERNEL_TMA) {
+        const int all[5][2] = {{128, 1}, {192, 1}, {64, 1}, {128, 2}, {192, 2}};
+        ncand = 0;
+        for (int out = 0; out < 2; ++out)
+            for (const auto& c : all)
+                if (lbm::sweep2_shape_ok(c[0], c[1], ctx->st) &&
+                    (out == lbm::OUT_STAGED || ctx->st == lbm::ST_F32)) {
+                    cand[ncand][0] = c[0];
+                    cand[ncand][1] = c[1];
+                    cand[ncand][2] = out;
+                    ++ncand;
+                }
+    }
+    for (int a = 0; a < ncand && ce == cudaSuccess && rc == LBM_OK; ++a) {
+        const int bx = cand[a][0], cpt = cand[a][1], out = cand[a][2];
+        const int per_sm = ctx->kernel != LBM_KERNEL_TMA
+                               ? 2
+                               : lbm::sweep2_blocks_per_sm(bx, cpt, out, ctx->kp.coupled, ctx->st);
         int segs[8];
         const int ns = seg_candidates(ctx->kp.nx, ctx->kp.ny, bx, per_sm, segs, 8);
         for (int k = 0; k < ns && rc == LBM_OK; ++k) {
-            rc = lbm_set_launch_shape(ctx, bx, segs[k]);
+            rc = set_shape(ctx, lbm::FusedShape{bx, segs[k], cpt, out});
             if (rc != LBM_OK) break;
             // twice the timed count first: captures the graphs the timed
             // steps replay, from either buffer parity
@@ -1230,7 +1408,7 @@ int lbm_autotune(lbm_ctx* ctx, int32_t steps, int32_t* tile_x, int32_t* seg_y,
             if (rc == LBM_OK) rc = cuda_fail(ctx, cudaEventElapsedTime(&ms, e0, e1));
             if (rc == LBM_OK && ms / steps < best) {
                 best = ms / steps;
-                best_shape = lbm::FusedShape{bx, segs[k]};
+                best_shape = lbm::FusedShape{bx, segs[k], cpt, out};
             }
             // put the state back before the next candidate
             ce = cudaMemcpy(state_alloc(ctx, cur0), snap, pop_bytes, cudaMemcpyDeviceToDevice);
@@ -1244,7 +1422,7 @@ int lbm_autotune(lbm_ctx* ctx, int32_t steps, int32_t* tile_x, int32_t* seg_y,
     if (e1) cudaEventDestroy(e1);
     cudaFree(snap);
     if (ce != cudaSuccess) return cuda_fail(ctx, ce);
-    const int rc2 = lbm_set_launch_shape(ctx, best_shape.bx, best_shape.seg);
+    const int rc2 = set_shape(ctx, best_shape);
     if (rc != LBM_OK) return rc;
     if (rc2 != LBM_OK) return rc2;
     if (tile_x) *tile_x = best_shape.bx;
@@ -1262,10 +1440,12 @@ int lbm_batch_autotune(lbm_batch* b, int32_t steps, int32_t* tile_x, int32_t* se
     float** snap = (float**)std::calloc((size_t)b->nruns, sizeof(float*));
     int* cur0 = (int*)std::calloc((size_t)b->nruns, sizeof(int));
     int64_t* step0 = (int64_t*)std::calloc((size_t)b->nruns, sizeof(int64_t));
-    if (!snap || !cur0 || !step0) {
+    lbm::FusedShape* run_shape = (lbm::FusedShape*)std::calloc((size_t)b->nruns, sizeof(lbm::FusedShape));
+    if (!snap || !cur0 || !step0 || !run_shape) {
         std::free(snap);
         std::free(cur0);
         std::free(step0);
+        std::free(run_shape);
         return LBM_ERR_NOMEM;
     }
     cudaError_t ce = cudaSuccess;
@@ -1281,36 +1461,78 @@ int lbm_batch_autotune(lbm_batch* b, int32_t steps, int32_t* tile_x, int32_t* se
             ce = cudaMemcpy(snap[r], b->runs[r]->pop_alloc[cur0[r]], bytes_of(r),
                             cudaMemcpyDeviceToDevice);
     }
-    const lbm::FusedShape shape0 = b->shape;
-    lbm::FusedShape best_shape = shape0;
-    double best = 1e300;
+    auto restore = [&]() {
+        for (int r = 0; r < b->nruns && ce == cudaSuccess; ++r) {
+            lbm_ctx* c = b->runs[r];
+            ce = cudaMemcpy(c->pop_alloc[cur0[r]], snap[r], bytes_of(r), cudaMemcpyDeviceToDevice);
+            c->cur = cur0[r];
+            c->step = step0[r];
+            sync_step_ctr(c);
+        }
+    };
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (ce == cudaSuccess) ce = cudaEventCreate(&e0);
     if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
-    const int bxs[3] = {128, 192, 64};
-    const int segs[7] = {16, 24, 32, 48, 64, 96, 128};
-    for (int a = 0; a < 3 && ce == cudaSuccess && rc == LBM_OK; ++a) {
-        for (int k = 0; k < 7 && rc == LBM_OK; ++k) {
-            rc = lbm_batch_set_launch_shape(b, bxs[a], segs[k]);
-            if (rc != LBM_OK) break;
-            // whole graphs, as long runs step: the first one builds the graph
-            rc = lbm_batch_step(b, GRAPH_STEPS);
-            if (rc == LBM_OK) rc = batch_fail(b, cudaEventRecord(e0, b->stream));
-            if (rc == LBM_OK) rc = lbm_batch_step(b, tsteps);
-            if (rc == LBM_OK) rc = batch_fail(b, cudaEventRecord(e1, b->stream));
-            if (rc == LBM_OK) rc = lbm_batch_synchronize(b);
-            float ms = 0.0f;
-            if (rc == LBM_OK) rc = batch_fail(b, cudaEventElapsedTime(&ms, e0, e1));
-            if (rc == LBM_OK && ms / tsteps < best) {
-                best = ms / tsteps;
-                best_shape = lbm::FusedShape{bxs[a], segs[k]};
+    // time the current form and shape: one graph of warm-up, then tsteps
+    auto time_it = [&](double& ms_step) -> int {
+        int r2 = lbm_batch_step(b, GRAPH_STEPS);
+        if (r2 == LBM_OK) r2 = batch_fail(b, cudaEventRecord(e0, b->stream));
+        if (r2 == LBM_OK) r2 = lbm_batch_step(b, tsteps);
+        if (r2 == LBM_OK) r2 = batch_fail(b, cudaEventRecord(e1, b->stream));
+        if (r2 == LBM_OK) r2 = lbm_batch_synchronize(b);
+        float ms = 0.0f;
+        if (r2 == LBM_OK) r2 = batch_fail(b, cudaEventElapsedTime(&ms, e0, e1));
+        ms_step = ms / tsteps;
+        restore();
+        return r2;
+    };
+    const int form0 = b->form;
+    const lbm::FusedShape shape0 = b->shape;
+    lbm::FusedShape best_shape = shape0;
+    int best_form = form0;
+    double best = 1e300;
+    // persistent form
+    b->form = LBM_BATCH_PERSISTENT;
+    const int cand[10][3] = {{128, 1, 0}, {192, 1, 0}, {64, 1, 0}, {128, 2, 0}, {192, 2, 0},
+                             {128, 1, 1}, {192, 1, 1}, {64, 1, 1}, {128, 2, 1}, {192, 2, 1}};
+    const int segs[4] = {16, 32, 48, 64};
+    for (int a = 0; a < 10 && ce == cudaSuccess && rc == LBM_OK; ++a) {
+        for (int k = 0; k < 4 && ce == cudaSuccess && rc == LBM_OK; ++k) {
+            b->shape = lbm::FusedShape{cand[a][0], segs[k], cand[a][1], cand[a][2]};
+            rc = batch_build_tiles(b);
+            double ms = 0.0;
+            if (rc == LBM_OK) rc = time_it(ms);
+            if (rc == LBM_OK && ms < best) {
+                best = ms;
+                best_form = LBM_BATCH_PERSISTENT;
+                best_shape = b->shape;
             }
-            for (int r = 0; r < b->nruns && ce == cudaSuccess; ++r) {
-                ce = cudaMemcpy(b->runs[r]->pop_alloc[cur0[r]], snap[r], bytes_of(r),
-                                cudaMemcpyDeviceToDevice);
-                b->runs[r]->cur = cur0[r];
-                b->runs[r]->step = step0[r];
+        }
+    }
+    // chains form: every grid size tuned on its first run, the shape shared
+    // by the runs of that size
+    if (ce == cudaSuccess && rc == LBM_OK) {
+        for (int r = 0; r < b->nruns && rc == LBM_OK; ++r) {
+            lbm_ctx* c = b->runs[r];
+            int src_run = -1;
+            for (int q = 0; q < r && src_run < 0; ++q)
+                if (b->runs[q]->kp.nx == c->kp.nx && b->runs[q]->kp.ny == c->kp.ny) src_run = q;
+            if (src_run >= 0) {
+                run_shape[r] = run_shape[src_run];
+            } else {
+                int tx = 0, sy = 0;
+                rc = lbm_autotune(c, 32, &tx, &sy, nullptr);
+                run_shape[r] = c->shape;
             }
+        }
+        for (int r = 0; r < b->nruns && rc == LBM_OK; ++r) rc = set_shape(b->runs[r], run_shape[r]);
+        b->form = LBM_BATCH_CHAINS;
+        batch_drop_graphs(b);
+        double ms = 0.0;
+        if (rc == LBM_OK) rc = time_it(ms);
+        if (rc == LBM_OK && ms < best) {
+            best = ms;
+            best_form = LBM_BATCH_CHAINS;
         }
     }
     if (e0) cudaEventDestroy(e0);
@@ -1319,10 +1541,17 @@ int lbm_batch_autotune(lbm_batch* b, int32_t steps, int32_t* tile_x, int32_t* se
     std::free(snap);
     std::free(cur0);
     std::free(step0);
+    std::free(run_shape);
     if (ce != cudaSuccess) return batch_fail(b, ce);
-    const int rc2 = lbm_batch_set_launch_shape(b, best_shape.bx, best_shape.seg);
     if (rc != LBM_OK) return rc;
-    if (rc2 != LBM_OK) return rc2;
+    // keep the winner: the persistent shape always; the runs' own shapes
+    // stay tuned if the chains form won, else follow the persistent shape
+    b->form = best_form;
+    b->shape = best_shape;
+    if (best_form == LBM_BATCH_PERSISTENT)
+        for (int r = 0; r < b->nruns && rc == LBM_OK; ++r) rc = set_shape(b->runs[r], best_shape);
+    if (rc == LBM_OK) rc = batch_build_tiles(b);
+    if (rc != LBM_OK) return rc;
     if (tile_x) *tile_x = best_shape.bx;
     if (seg_y) *seg_y = best_shape.seg;
     if (ms_per_step) *ms_per_step = best;

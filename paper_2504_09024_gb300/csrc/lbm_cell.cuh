@@ -11,16 +11,27 @@ namespace lbm {
 // shared helpers
 // ---------------------------------------------------------------------------
 
-__device__ __forceinline__ float sum9(const float a[9]) {
+template <class V>
+__device__ __forceinline__ V sum9(const V a[9]) {
     return ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7])) + a[8];
 }
 
-__device__ __forceinline__ float lerp_phase(const KParams& p, float phi, float va, float vb) {
-    return vb + (phi - p.phi_b) * p.inv_dphi * (va - vb);
+template <class V>
+__device__ __forceinline__ V lerp_phase(const KParams& p, V phi, float va, float vb) {
+    return vb + ((va - vb) * p.inv_dphi) * (phi - p.phi_b);
 }
 
-__device__ __forceinline__ float rate_from_coeff(float coeff) {
-    return 1.0f / (coeff * 3.0f + 0.5f);
+template <class V>
+__device__ __forceinline__ V rate_from_coeff(V coeff) {
+    return vmap(coeff, [](float c) { return 1.0f / (c * 3.0f + 0.5f); });
+}
+
+template <class V>
+__device__ __forceinline__ V vdiv(V a, V b) {
+    V q;
+#pragma unroll
+    for (int k = 0; k < Lanes<V>::n; ++k) set_lane(q, k, lane(a, k) / lane(b, k));
+    return q;
 }
 
 // Deviation-form equilibrium of the flow lattice without source: shifted
@@ -80,54 +91,66 @@ __device__ __forceinline__ void load3x3_fx(const float* __restrict__ F, const KP
     }
 }
 
-// Local values and stencil results one cell's collisions need.
-struct CellGeom {
-    int phi_fx;                  // phi in fixed point (exact interface factors)
-    float phi, c, sig, dps;      // zeroth moments, sigma(c), P* - P0
-    float nx, ny, gm;            // unit normal, |grad phi|
-    float kappa;                 // div n
-    float sgx, sgy;              // grad sigma
-    float pgx, pgy;              // grad (P* - P0)
-    float fgx, fgy;              // grad phi (for grad rho)
+// Local values and stencil results one cell's (or two cells') collisions need.
+template <class V, class VI = typename Lanes<V>::I>
+struct CellGeomT {
+    VI phi_fx;               // phi in fixed point (exact interface factors)
+    V phi, c, sig, dps;      // zeroth moments, sigma(c), P* - P0
+    V nx, ny, gm;            // unit normal, |grad phi|
+    V kappa;                 // div n
+    V sgx, sgy;              // grad sigma
+    V pgx, pgy;              // grad (P* - P0)
+    V fgx, fgy;              // grad phi (for grad rho)
 };
+using CellGeom = CellGeomT<float>;
 
-struct CellOut {
-    float ux, uy, dP;
+template <class V>
+struct CellOutT {
+    V ux, uy, dP;
 };
+using CellOut = CellOutT<float>;
 
 // Flow part of one cell's collisions (App. D): forces, velocity, pressure
 // and, with do_collide, the flow populations gg collided in place.
 // out_scale: power-of-two factor on the output populations (16-bit storage).
-__device__ __forceinline__ CellOut collide_flow_cell(const KParams& p, const CellGeom& g, int j,
-                                                     float gg[9], bool do_collide,
-                                                     float out_scale = 1.0f) {
-    CellOut o;
+template <class V>
+__device__ __forceinline__ CellOutT<V> collide_flow_cell(const KParams& p, const CellGeomT<V>& g,
+                                                         int j, V gg[9], bool do_collide,
+                                                         float out_scale = 1.0f) {
+    CellOutT<V> o;
     // surface-tension force, Eq. (Fs)
-    const float g2 = g.gm * g.gm;
-    const float nds = g.nx * g.sgx + g.ny * g.sgy;
-    const float Fsx = p.N_sigma * g2 * (-g.sig * g.kappa * g.nx + (g.sgx - g.nx * nds));
-    const float Fsy = p.N_sigma * g2 * (-g.sig * g.kappa * g.ny + (g.sgy - g.ny * nds));
-    const float Ftx = Fsx + p.fext_x, Fty = Fsy + p.fext_y;
-    const float rho = p.rho_uniform ? p.rho_a : lerp_phase(p, g.phi, p.rho_a, p.rho_b);
-    const float jx = (gg[1] - gg[3]) + (gg[5] - gg[6]) - (gg[7] - gg[8]);
-    const float jy = (gg[2] - gg[4]) + (gg[5] + gg[6]) - (gg[7] + gg[8]);
-    // cs2 rho u = sum e g + cs2 F_t / 2  (App. D).  The division uses the
-    // same rounded rho cs2 as the equilibrium, so j -> u -> rho cs2 u does
-    // not drift by the rounding of 1/3 every step.
-    const float R = rho * CS2;
-    o.ux = (jx + 0.5f * CS2 * Ftx) / R;
-    o.uy = (jy + 0.5f * CS2 * Fty) / R;
-    // F_p = -grad psi with psi = P* - rho cs2
-    float Fpx = -g.pgx, Fpy = -g.pgy;
-    if (!p.rho_uniform) {
-        const float drho = (p.rho_a - p.rho_b) * p.inv_dphi;
-        Fpx += CS2 * drho * g.fgx;
-        Fpy += CS2 * drho * g.fgy;
+    const V g2n = p.N_sigma * (g.gm * g.gm);
+    const V nds = g.nx * g.sgx + g.ny * g.sgy;
+    const V sk = g.sig * g.kappa;
+    const V Fsx = g2n * ((g.sgx - g.nx * nds) - sk * g.nx);
+    const V Fsy = g2n * ((g.sgy - g.ny * nds) - sk * g.ny);
+    const V Ftx = Fsx + p.fext_x, Fty = Fsy + p.fext_y;
+    const V rho = p.rho_uniform ? vsplat<V>(p.rho_a) : lerp_phase(p, g.phi, p.rho_a, p.rho_b);
+    const V jx = ((gg[1] - gg[3]) + (gg[5] - gg[6])) - (gg[7] - gg[8]);
+    const V jy = ((gg[2] - gg[4]) + (gg[5] + gg[6])) - (gg[7] + gg[8]);
+    // cs2 rho u = sum e g + cs2 F_t / 2  (App. D), with the same rounded
+    // rho cs2 as the equilibrium.
+    const V R = rho * CS2;
+    if (p.rho_uniform) {
+        // one density: multiply by the reciprocal of the same rounded rho cs2
+        const float iR = 1.0f / (p.rho_a * CS2);
+        o.ux = vfma(0.5f * CS2, Ftx, jx) * iR;
+        o.uy = vfma(0.5f * CS2, Fty, jy) * iR;
+    } else {
+        o.ux = vdiv(vfma(0.5f * CS2, Ftx, jx), R);
+        o.uy = vdiv(vfma(0.5f * CS2, Fty, jy), R);
     }
-    const float G = Fpx * o.ux + Fpy * o.uy;
-    o.dP = g.dps + 0.5f * G;  // P = sum g + sigma_00 / 2
+    // F_p = -grad psi with psi = P* - rho cs2
+    V Fpx = -g.pgx, Fpy = -g.pgy;
+    if (!p.rho_uniform) {
+        const float drho = CS2 * (p.rho_a - p.rho_b) * p.inv_dphi;
+        Fpx = vfma(drho, g.fgx, Fpx);
+        Fpy = vfma(drho, g.fgy, Fpy);
+    }
+    const V G = Fpx * o.ux + Fpy * o.uy;
+    o.dP = vfma(0.5f, G, g.dps);  // P = sum g + sigma_00 / 2
     if (do_collide) {
-        FlowMacro m;
+        FlowMacroT<V> m;
         m.ux = o.ux;
         m.uy = o.uy;
         m.rho = rho;
@@ -137,7 +160,7 @@ __device__ __forceinline__ CellOut collide_flow_cell(const KParams& p, const Cel
         m.Fty = Fty;
         m.Fpx = Fpx;
         m.Fpy = Fpy;
-        m.w_nu = p.nu_uniform ? p.w_nu : rate_from_coeff(lerp_phase(p, g.phi, p.nu_a, p.nu_b));
+        m.w_nu = p.nu_uniform ? vsplat<V>(p.w_nu) : rate_from_coeff(lerp_phase(p, g.phi, p.nu_a, p.nu_b));
         collide_flow(gg, m, p.w_zeta, out_scale);
         wall_correct_flow(gg, p, j, rho, out_scale);
     }
@@ -147,18 +170,17 @@ __device__ __forceinline__ CellOut collide_flow_cell(const KParams& p, const Cel
 // Scalar part of one cell's collisions: f (Sec. 3, App. C) and h (Sec. 2.2)
 // given the velocity; f and h enter as their first moments (the zeroth
 // moments are phi and c) and leave in deviation form df, dh (q = 1..8).
-__device__ __forceinline__ void collide_scalars_cell(const KParams& p, int phi_fx, float phi,
-                                                     float c, float nx, float ny, float ux,
-                                                     float uy, float fjx, float fjy, float hjx,
-                                                     float hjy, float df[9], float dh[9],
-                                                     float sf = 1.0f, float sh = 1.0f) {
+template <class V, class VI>
+__device__ __forceinline__ void collide_scalars_cell(const KParams& p, VI phi_fx, V phi, V c, V nx,
+                                                     V ny, V ux, V uy, V fjx, V fjy, V hjx, V hjy,
+                                                     V df[9], V dh[9], float sf = 1.0f,
+                                                     float sh = 1.0f) {
     // Eq. (theta) and the theta_c of Eq. (ISS)
-    float theta, theta_c;
+    V theta, theta_c;
     interface_coeffs(p, phi_fx, c, theta, theta_c);
-    collide_scalar_dev(phi, fjx, fjy, p.M_phi * theta * nx, p.M_phi * theta * ny, p.w_kappa, ux,
-                       uy, df, sf);
-    collide_scalar_dev(c, hjx, hjy, p.D_s * theta_c * nx, p.D_s * theta_c * ny, p.w_chi, ux, uy,
-                       dh, sh);
+    const V mt = p.M_phi * theta, dt = p.D_s * theta_c;
+    collide_scalar_dev(phi, fjx, fjy, mt * nx, mt * ny, p.w_kappa, ux, uy, df, sf);
+    collide_scalar_dev(c, hjx, hjy, dt * nx, dt * ny, p.w_chi, ux, uy, dh, sh);
 }
 
 // The three collisions of one cell at row j.  f and h enter as their first

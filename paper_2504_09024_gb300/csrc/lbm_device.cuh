@@ -23,6 +23,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "lbm_vec.cuh"
+
 namespace lbm {
 
 constexpr float CS2 = 1.0f / 3.0f;
@@ -175,6 +177,55 @@ __device__ __forceinline__ int fx_add(int s0, float inc, float scale) {
     return r + (unsigned)FX_RANGE > 2u * (unsigned)FX_RANGE ? FX_INVALID : (int)r;
 }
 
+// Counter-based hash for the stochastic roundings: the PCG hash of Jarzynski
+// and Olano, "Hash Functions for GPU Rendering", JCGT 9(3), 2020 (the output
+// permutation of the PCG generator, O'Neill 2014, applied to one LCG step of
+// the input).
+__device__ __forceinline__ uint32_t pcg_hash(uint32_t v) {
+    const uint32_t state = v * 747796405u + 2891336453u;
+    const uint32_t word = ((state >> ((state >> 28u) + 4u)) ^ state) * 277803737u;
+    return (word >> 22u) ^ word;
+}
+
+// Seed of one step's roundings: the step about to be taken is the device
+// counter plus the launch's offset within its graph.
+__device__ __forceinline__ uint32_t step_seed(const KParams& p) {
+    return pcg_hash((p.step_ctr ? __ldg(p.step_ctr) : 0u) + (uint32_t)p.step_off);
+}
+
+// Random bits of cell (i, j) in one step: the step's hash offset by a Weyl
+// sequence over the cells (the golden-ratio increment).  For every cell the
+// bits are uniform over steps (the step hash is), and within a step they are
+// spread evenly over the cells; one multiply-add per cell.
+__device__ __forceinline__ uint32_t cell_bits(uint32_t seed, int i, int j, int nx) {
+    return seed + 0x9E3779B9u * (uint32_t)(j * nx + i);
+}
+
+// 32 random bits of cell (i, j) for the roundings of its zeroth moments
+// (f: the high 16 bits, h: the low 16 bits).
+__device__ __forceinline__ uint32_t moment_bits(uint32_t seed, int i, int j, int nx) {
+    return cell_bits(seed ^ 0x5bd1e995u, i, j, nx);
+}
+
+// Fixed-point value after adding a float increment, rounded stochastically:
+// up with probability equal to the dropped fraction, drawn from the high 16
+// bits of r16.  Rounding to nearest drops every increment below half a unit,
+// and in the tails of the interface profiles, where the increments are tiny
+// and of one sign step after step, that bias moves the totals of phi and c;
+// the zero-mean rounding keeps them (to the random walk of the roundings).
+__device__ __forceinline__ int fx_add_sr(int s0, float inc, float scale, uint32_t r16) {
+    const float v = inc * scale;
+    if (!(fabsf(v) < 1.0e9f)) return FX_INVALID;
+    const float u = (float)(r16 >> 16) * (1.0f / 65536.0f) + (1.0f / 131072.0f);
+    const unsigned r = (unsigned)s0 + (unsigned)__float2int_rd(v + u);
+    return r + (unsigned)FX_RANGE > 2u * (unsigned)FX_RANGE ? FX_INVALID : (int)r;
+}
+__device__ __forceinline__ i2 fx_add_sr(i2 s0, f2 inc, float scale, uint32_t ra, uint32_t rb) {
+    return i2{fx_add_sr(s0.x, inc.x, scale, ra), fx_add_sr(s0.y, inc.y, scale, rb)};
+}
+// The bits of the h lattice's rounding, from the same cell draw.
+__device__ __forceinline__ uint32_t second_bits(uint32_t b) { return b << 16; }
+
 // Float value of a fixed-point number (NaN for the invalid marker).
 __device__ __forceinline__ double fx_to_double(int s, float scale) {
     return s == FX_INVALID ? __longlong_as_double(0x7ff8000000000000ll) : (double)s / (double)scale;
@@ -280,24 +331,26 @@ __device__ __forceinline__ void pull9_dev(const float* __restrict__ base, const 
 }
 
 // Isotropic gradient of a fixed-point field from exact integer differences.
-__device__ __forceinline__ void iso_grad_fx(const int v[3][3], float inv, float& gx, float& gy) {
-    gx = ((1.0f / 3.0f) * (float)(v[1][2] - v[1][0]) +
-          (1.0f / 12.0f) * ((float)(v[2][2] - v[2][0]) + (float)(v[0][2] - v[0][0]))) * inv;
-    gy = ((1.0f / 3.0f) * (float)(v[2][1] - v[0][1]) +
-          (1.0f / 12.0f) * ((float)(v[2][2] - v[0][2]) + (float)(v[2][0] - v[0][0]))) * inv;
+template <class V, class VI>
+__device__ __forceinline__ void iso_grad_fx(const VI v[3][3], float inv, V& gx, V& gy) {
+    gx = ((1.0f / 3.0f) * i2f(isub(v[1][2], v[1][0])) +
+          (1.0f / 12.0f) * (i2f(isub(v[2][2], v[2][0])) + i2f(isub(v[0][2], v[0][0])))) * inv;
+    gy = ((1.0f / 3.0f) * i2f(isub(v[2][1], v[0][1])) +
+          (1.0f / 12.0f) * (i2f(isub(v[2][2], v[0][2])) + i2f(isub(v[2][0], v[0][0])))) * inv;
 }
 
 // theta (Eq. theta) and theta_c (Eq. ISS) from the fixed-point phi: the
 // factors phi_a - phi, phi - phi_b and phi_m - phi are exact integer
 // differences before the conversion to float.
-__device__ __forceinline__ void interface_coeffs(const KParams& p, int phi_fx, float c, float& theta,
-                                                 float& theta_c) {
+template <class V, class VI>
+__device__ __forceinline__ void interface_coeffs(const KParams& p, VI phi_fx, V c, V& theta,
+                                                 V& theta_c) {
     const float inv = p.fx_inv[0];
-    const float A = (float)(p.phi_a_fx - phi_fx) * inv;
-    const float B = (float)(phi_fx - p.phi_b_fx) * inv;
-    const float M = (float)(p.phi_m_fx - phi_fx) * inv;
-    theta = p.four_over_W * A * B * p.inv_dphi;
-    theta_c = p.eight_over_W * c * M * p.inv_dphi;
+    const V A = i2f(isub(p.phi_a_fx, phi_fx)) * inv;
+    const V B = i2f(isub(phi_fx, p.phi_b_fx)) * inv;
+    const V M = i2f(isub(p.phi_m_fx, phi_fx)) * inv;
+    theta = (p.four_over_W * p.inv_dphi) * (A * B);
+    theta_c = (p.eight_over_W * p.inv_dphi) * (c * M);
 }
 
 // ---------------------------------------------------------------------------
@@ -305,7 +358,8 @@ __device__ __forceinline__ void interface_coeffs(const KParams& p, int phi_fx, f
 // ---------------------------------------------------------------------------
 
 // Isotropic gradient (1/cs2) sum_q w_q e_q A(x + e_q).
-__device__ __forceinline__ void iso_grad(const float v[3][3], float& gx, float& gy) {
+template <class V>
+__device__ __forceinline__ void iso_grad(const V v[3][3], V& gx, V& gy) {
     gx = (1.0f / 3.0f) * (v[1][2] - v[1][0]) +
          (1.0f / 12.0f) * ((v[2][2] - v[2][0]) + (v[0][2] - v[0][0]));
     gy = (1.0f / 3.0f) * (v[2][1] - v[0][1]) +
@@ -313,18 +367,20 @@ __device__ __forceinline__ void iso_grad(const float v[3][3], float& gx, float& 
 }
 
 // Isotropic divergence of a vector field given on the 3x3 neighbourhood.
-__device__ __forceinline__ float iso_div(const float vx[3][3], const float vy[3][3]) {
-    float dxx = (1.0f / 3.0f) * (vx[1][2] - vx[1][0]) +
-                (1.0f / 12.0f) * ((vx[2][2] - vx[2][0]) + (vx[0][2] - vx[0][0]));
-    float dyy = (1.0f / 3.0f) * (vy[2][1] - vy[0][1]) +
-                (1.0f / 12.0f) * ((vy[2][2] + vy[2][0]) - (vy[0][2] + vy[0][0]));
+template <class V>
+__device__ __forceinline__ V iso_div(const V vx[3][3], const V vy[3][3]) {
+    const V dxx = (1.0f / 3.0f) * (vx[1][2] - vx[1][0]) +
+                  (1.0f / 12.0f) * ((vx[2][2] - vx[2][0]) + (vx[0][2] - vx[0][0]));
+    const V dyy = (1.0f / 3.0f) * (vy[2][1] - vy[0][1]) +
+                  (1.0f / 12.0f) * ((vy[2][2] + vy[2][0]) - (vy[0][2] + vy[0][0]));
     return dxx + dyy;
 }
 
-__device__ __forceinline__ void unit_normal(float gx, float gy, float& nx, float& ny, float& mag) {
+template <class V>
+__device__ __forceinline__ void unit_normal(V gx, V gy, V& nx, V& ny, V& mag) {
     // branch-free: below the threshold the normal and the magnitude are 0
-    const float g2 = gx * gx + gy * gy;
-    const float inv = g2 > EPS_N * EPS_N ? rsqrtf(g2) : 0.0f;  // rsqrt within 2 ulp
+    const V g2 = gx * gx + gy * gy;
+    const V inv = vmap(g2, [](float v) { return v > EPS_N * EPS_N ? rsqrtf(v) : 0.0f; });
     nx = gx * inv;
     ny = gy * inv;
     mag = g2 * inv;
@@ -333,9 +389,11 @@ __device__ __forceinline__ void unit_normal(float gx, float gy, float& nx, float
 // Langmuir isotherm, Eq. (EOS).  beta = 0 (clean interface) gives sigma_o
 // whatever c is: 0 * log(<= 0) would be NaN once a passive surfactant reaches
 // c_max, so the product is selected away rather than formed.
-__device__ __forceinline__ float sigma_of_c(const KParams& p, float c) {
-    const float t = p.beta * __logf(1.0f - c * p.inv_cmax);
-    return p.sigma_o * (1.0f + (p.beta != 0.0f ? t : 0.0f));
+template <class V>
+__device__ __forceinline__ V sigma_of_c(const KParams& p, V c) {
+    if (p.beta == 0.0f) return vsplat<V>(p.sigma_o);
+    const V t = vmap(1.0f - c * p.inv_cmax, [](float v) { return __logf(v); });
+    return p.sigma_o + (p.sigma_o * p.beta) * t;
 }
 
 // ---------------------------------------------------------------------------
@@ -345,10 +403,11 @@ __device__ __forceinline__ float sigma_of_c(const KParams& p, float c) {
 // P^-1 applied to raw moments r = (00,10,01,20,02,11,21,12,22) (App. A),
 // times s (a power of two: the 16-bit storage scale, folded into the factors
 // 1/2 and 1/4 at no cost and without rounding; 1 for FP32 storage).
-__device__ __forceinline__ void raw_to_pops(const float r[9], float out[9], float s = 1.0f) {
+template <class V>
+__device__ __forceinline__ void raw_to_pops(const V r[9], V out[9], float s = 1.0f) {
     // factored: the eight pair sums and differences are shared by two outputs each
-    const float a = r[3] - r[8], b = r[1] - r[7], c = r[4] - r[8], d = r[2] - r[6];
-    const float e = r[8] + r[5], f = r[6] + r[7], g = r[8] - r[5], h = r[6] - r[7];
+    const V a = r[3] - r[8], b = r[1] - r[7], c = r[4] - r[8], d = r[2] - r[6];
+    const V e = r[8] + r[5], f = r[6] + r[7], g = r[8] - r[5], h = r[6] - r[7];
     const float h2 = 0.5f * s, h4 = 0.25f * s;
     out[0] = ((r[0] - r[3]) - c) * s;
     out[1] = h2 * (a + b);
@@ -362,8 +421,9 @@ __device__ __forceinline__ void raw_to_pops(const float r[9], float out[9], floa
 }
 
 // F^-1(u) applied to central moments k (binomial expansion of ((e-u)+u)^m).
-__device__ __forceinline__ void central_to_raw(const float k[9], float ux, float uy, float r[9]) {
-    const float ux2 = ux * ux, uy2 = uy * uy, uxy = ux * uy;
+template <class V>
+__device__ __forceinline__ void central_to_raw(const V k[9], V ux, V uy, V r[9]) {
+    const V ux2 = ux * ux, uy2 = uy * uy, uxy = ux * uy;
     r[0] = k[0];
     r[1] = ux * k[0] + k[1];
     r[2] = uy * k[0] + k[2];
@@ -379,28 +439,56 @@ __device__ __forceinline__ void central_to_raw(const float k[9], float ux, float
 // The same transform as central_to_raw, applied as two one-dimensional shifts
 // (F^-1(u) is the tensor product of the x and y binomial shifts): per order-2
 // triple (c0, c1, c2) -> (c0, c1 + u c0, c2 + u (c1 + (c1 + u c0))).
-__device__ __forceinline__ void central_to_raw_sep(const float k[9], float ux, float uy,
-                                                   float r[9]) {
+template <class V>
+__device__ __forceinline__ void central_to_raw_sep(const V k[9], V ux, V uy, V r[9]) {
     // x shift of the rows b = 0, 1, 2 (k indices: 00 0, 10 1, 20 3 | 01 2, 11 5, 21 6 | 02 4, 12 7, 22 8)
-    const float m10 = k[1] + ux * k[0], m20 = k[3] + ux * (k[1] + m10);
-    const float m11 = k[5] + ux * k[2], m21 = k[6] + ux * (k[5] + m11);
-    const float m12 = k[7] + ux * k[4], m22 = k[8] + ux * (k[7] + m12);
+    const V m10 = vfma(ux, k[0], k[1]), m20 = vfma(ux, k[1] + m10, k[3]);
+    const V m11 = vfma(ux, k[2], k[5]), m21 = vfma(ux, k[5] + m11, k[6]);
+    const V m12 = vfma(ux, k[4], k[7]), m22 = vfma(ux, k[7] + m12, k[8]);
     // y shift of the columns a = 0, 1, 2
     r[0] = k[0];
-    r[2] = k[2] + uy * k[0];
-    r[4] = k[4] + uy * (k[2] + r[2]);
+    r[2] = vfma(uy, k[0], k[2]);
+    r[4] = vfma(uy, k[2] + r[2], k[4]);
     r[1] = m10;
-    r[5] = m11 + uy * m10;
-    r[7] = m12 + uy * (m11 + r[5]);
+    r[5] = vfma(uy, m10, m11);
+    r[7] = vfma(uy, m11 + r[5], m12);
     r[3] = m20;
-    r[6] = m21 + uy * m20;
-    r[8] = m22 + uy * (m21 + r[6]);
+    r[6] = vfma(uy, m20, m21);
+    r[8] = vfma(uy, m21 + r[6], m22);
 }
 
-// Advection-diffusion lattice (f with s = phi, q = M_phi theta n; or h with
-// s = c, q = D_s theta_c n): all central moments are set to their equilibria
-// (s, q, cs2 s, cs2 s, 0, 0, 0, cs4 s) except the first-order ones, which
-// relax at rate w.  In/out: pre-/post-collision populations.
+// Advection-diffusion collision returning deviation-form output:
+// d_q = a~_q - w_q s for q = 1..8 (a~ = P^-1 F^-1(u) k), where all central
+// moments are set to their equilibria (s, q, cs2 s, cs2 s, 0, 0, 0, cs4 s)
+// except the first-order ones, which relax at rate w (f with s = phi,
+// q = M_phi theta n; h with s = c, q = D_s theta_c n).  The raw moments of
+// the deviation are s (raw moments of the equilibrium shape at u minus those
+// at rest) plus the raw moments of F^-1(u) (0, k10~, k01~, 0, ...), so no
+// O(s) term is formed.
+template <class V, class W>
+__device__ __forceinline__ void collide_scalar_dev(V s, V jx, V jy, V qx, V qy, W w, V ux, V uy,
+                                                   V d[9], float out_scale = 1.0f) {
+    const V k10 = jx - ux * s, k01 = jy - uy * s;
+    const V a = vfma(w, qx - k10, k10);
+    const V b = vfma(w, qy - k01, k01);
+    const V ux2 = ux * ux, uy2 = uy * uy, uxy = ux * uy;
+    const V su = s * ux, sv = s * uy;
+    V R[9];
+    R[0] = vsplat<V>(0.0f);
+    R[1] = su + a;
+    R[2] = sv + b;
+    R[3] = vfma(su, ux, 2.0f * (ux * a));
+    R[4] = vfma(sv, uy, 2.0f * (uy * b));
+    R[5] = vfma(su, uy, vfma(uy, a, ux * b));
+    R[6] = vfma(sv, ux2 + CS2, uxy * (2.0f * a) + ux2 * b);
+    R[7] = vfma(su, uy2 + CS2, uy2 * a + uxy * (2.0f * b));
+    R[8] = vfma(s, ux2 * uy2 + CS2 * (ux2 + uy2), 2.0f * (uxy * (uy * a + ux * b)));
+    raw_to_pops(R, d, out_scale);
+}
+
+// Advection-diffusion collision on full populations (initialisation and the
+// cross-check kernels): all central moments to equilibrium except the first
+// order, which relaxes at rate w.  In/out: pre-/post-collision populations.
 __device__ __forceinline__ void collide_scalar(float a[9], float s, float qx, float qy, float w,
                                                float ux, float uy) {
     const float jx = (a[1] - a[3]) + (a[5] - a[6]) - (a[7] - a[8]);
@@ -421,40 +509,18 @@ __device__ __forceinline__ void collide_scalar(float a[9], float s, float qx, fl
     raw_to_pops(r, a);
 }
 
-// Same collision returning deviation-form output: d_q = a~_q - w_q s for
-// q = 1..8 (a~ = P^-1 F^-1(u) k).  The raw moments of the deviation are
-// s (raw moments of the equilibrium shape at u minus those at rest) plus the
-// raw moments of F^-1(u) (0, k10~, k01~, 0, ...), so no O(s) term is formed.
-__device__ __forceinline__ void collide_scalar_dev(float s, float jx, float jy, float qx, float qy,
-                                                   float w, float ux, float uy, float d[9],
-                                                   float out_scale = 1.0f) {
-    const float k10 = jx - ux * s, k01 = jy - uy * s;
-    const float a = k10 + w * (qx - k10);
-    const float b = k01 + w * (qy - k01);
-    const float ux2 = ux * ux, uy2 = uy * uy, uxy = ux * uy;
-    float R[9];
-    R[0] = 0.0f;
-    R[1] = s * ux + a;
-    R[2] = s * uy + b;
-    R[3] = s * ux2 + 2.0f * ux * a;
-    R[4] = s * uy2 + 2.0f * uy * b;
-    R[5] = s * uxy + uy * a + ux * b;
-    R[6] = s * (ux2 * uy + uy * CS2) + 2.0f * uxy * a + ux2 * b;
-    R[7] = s * (ux * uy2 + ux * CS2) + uy2 * a + 2.0f * uxy * b;
-    R[8] = s * (ux2 * uy2 + CS2 * (ux2 + uy2)) + 2.0f * ux * uy2 * a + 2.0f * ux2 * uy * b;
-    raw_to_pops(R, d, out_scale);
-}
-
-// Macroscopic inputs of the flow collision at one cell.
-struct FlowMacro {
-    float ux, uy;      // velocity
-    float rho;         // density
-    float dP;          // P - P0 (after the half-source correction)
-    float dPs;         // sum of shifted g = P* - P0
-    float Ftx, Fty;    // total force F_s + F_ext
-    float Fpx, Fpy;    // pressure force -grad psi
-    float w_nu;        // shear relaxation rate
+// Macroscopic inputs of the flow collision at one cell (or two).
+template <class V>
+struct FlowMacroT {
+    V ux, uy;      // velocity
+    V rho;         // density
+    V dP;          // P - P0 (after the half-source correction)
+    V dPs;         // sum of shifted g = P* - P0
+    V Ftx, Fty;    // total force F_s + F_ext
+    V Fpx, Fpy;    // pressure force -grad psi
+    V w_nu;        // shear relaxation rate
 };
+using FlowMacro = FlowMacroT<float>;
 
 // Flow lattice, Eq. (centralmomentLBE2fluidflow), on shifted populations
 // a = g - w P0.  Central moments of the shift are P0 W(u) with W(u) the
@@ -462,51 +528,53 @@ struct FlowMacro {
 // collision runs on deviations: d_eta^eq = rho cs2 (M(u) - W(u)) + dP W(u).
 // out_scale: power-of-two factor applied to the output populations (16-bit
 // storage scale; 1 for FP32 storage).
-__device__ __forceinline__ void collide_flow(float a[9], const FlowMacro& m, float w_zeta,
+template <class V>
+__device__ __forceinline__ void collide_flow(V a[9], const FlowMacroT<V>& m, float w_zeta,
                                              float out_scale = 1.0f) {
-    const float ux = m.ux, uy = m.uy;
-    const float ux2 = ux * ux, uy2 = uy * uy, uxy = ux * uy;
+    const V ux = m.ux, uy = m.uy;
+    const V ux2 = ux * ux, uy2 = uy * uy, uxy = ux * uy;
     // raw moments of the shifted populations that relax at non-unit rates
-    const float jx = (a[1] - a[3]) + (a[5] - a[6]) - (a[7] - a[8]);
-    const float jy = (a[2] - a[4]) + (a[5] + a[6]) - (a[7] + a[8]);
-    const float corner = (a[5] + a[6]) + (a[7] + a[8]);
-    const float r20 = (a[1] + a[3]) + corner;
-    const float r02 = (a[2] + a[4]) + corner;
-    const float r11 = (a[5] - a[6]) + (a[7] - a[8]);
-    const float s0 = m.dPs;
+    const V d56 = a[5] - a[6], d78 = a[7] - a[8], s56 = a[5] + a[6], s78 = a[7] + a[8];
+    const V jx = ((a[1] - a[3]) + d56) - d78;
+    const V jy = ((a[2] - a[4]) + s56) - s78;
+    const V corner = s56 + s78;
+    const V r20 = (a[1] + a[3]) + corner;
+    const V r02 = (a[2] + a[4]) + corner;
+    const V r11 = d56 + d78;
+    const V s0 = m.dPs;
     // pre-collision central moments (deviation form)
-    const float e20 = r20 - 2.0f * ux * jx + ux2 * s0;
-    const float e02 = r02 - 2.0f * uy * jy + uy2 * s0;
-    const float e11 = r11 - uy * jx - ux * jy + uxy * s0;
-    // equilibria (deviation form); A9 sign reading: first order -psi u
-    const float R = m.rho * CS2, dP = m.dP;
-    const float RmP = R - dP;
-    const float q20 = -R * ux2 + dP * (CS2 + ux2);
-    const float q02 = -R * uy2 + dP * (CS2 + uy2);
-    const float q11 = -RmP * uxy;
+    const V e20 = vfma(ux2, s0, r20 - 2.0f * (ux * jx));
+    const V e02 = vfma(uy2, s0, r02 - 2.0f * (uy * jy));
+    const V e11 = vfma(uxy, s0, r11 - (uy * jx + ux * jy));
+    // equilibria (deviation form); first order -psi u (the sign reading of App. D)
+    const V R = m.rho * CS2, dP = m.dP;
+    const V RmP = R - dP;
+    const V q20 = vfma(dP, ux2 + CS2, -(R * ux2));
+    const V q02 = vfma(dP, uy2 + CS2, -(R * uy2));
+    const V q11 = -(RmP * uxy);
     // source central moments (App. D)
-    const float G = m.Fpx * ux + m.Fpy * uy;
-    const float s10 = CS2 * m.Ftx - ux * G;
-    const float s01 = CS2 * m.Fty - uy * G;
-    const float s20 = 2.0f * CS2 * m.Fpx * ux + (ux2 + CS2) * G;
-    const float s02 = 2.0f * CS2 * m.Fpy * uy + (uy2 + CS2) * G;
-    const float s11 = CS2 * (m.Fpx * uy + m.Fpy * ux) + uxy * G;
+    const V G = m.Fpx * ux + m.Fpy * uy;
+    const V s10 = CS2 * m.Ftx - ux * G;
+    const V s01 = CS2 * m.Fty - uy * G;
+    const V s20 = vfma(ux2 + CS2, G, (2.0f * CS2) * (m.Fpx * ux));
+    const V s02 = vfma(uy2 + CS2, G, (2.0f * CS2) * (m.Fpy * uy));
+    const V s11 = vfma(uxy, G, CS2 * (m.Fpx * uy + m.Fpy * ux));
     // relax in the combined basis (B): 2s at w_zeta, 2d and 11 at w_nu, rest at 1
-    const float wn = m.w_nu;
-    const float h2s = e20 + e02, h2d = e20 - e02;
-    const float t2s = h2s + w_zeta * ((q20 + q02) - h2s) + (1.0f - 0.5f * w_zeta) * (s20 + s02);
-    const float t2d = h2d + wn * ((q20 - q02) - h2d) + (1.0f - 0.5f * wn) * (s20 - s02);
-    float k[9];
-    k[0] = dP + 0.5f * G;
-    k[1] = ux * RmP + 0.5f * s10;
-    k[2] = uy * RmP + 0.5f * s01;
+    const V wn = m.w_nu;
+    const V h2s = e20 + e02, h2d = e20 - e02;
+    const V t2s = vfma(w_zeta, (q20 + q02) - h2s, h2s) + (1.0f - 0.5f * w_zeta) * (s20 + s02);
+    const V t2d = vfma(wn, (q20 - q02) - h2d, h2d) + (1.0f - 0.5f * wn) * (s20 - s02);
+    V k[9];
+    k[0] = vfma(0.5f, G, dP);
+    k[1] = vfma(ux, RmP, 0.5f * s10);
+    k[2] = vfma(uy, RmP, 0.5f * s01);
     k[3] = 0.5f * (t2s + t2d);
     k[4] = 0.5f * (t2s - t2d);
-    k[5] = e11 + wn * (q11 - e11) + (1.0f - 0.5f * wn) * s11;
-    k[6] = RmP * (ux2 + CS2) * uy;
-    k[7] = RmP * (uy2 + CS2) * ux;
-    k[8] = -R * (ux2 * uy2 + CS2 * (ux2 + uy2)) + dP * (ux2 + CS2) * (uy2 + CS2);
-    float r[9];
+    k[5] = vfma(wn, q11 - e11, e11) + (1.0f - 0.5f * wn) * s11;
+    k[6] = RmP * ((ux2 + CS2) * uy);
+    k[7] = RmP * ((uy2 + CS2) * ux);
+    k[8] = vfma(dP, (ux2 + CS2) * (uy2 + CS2), -(R * vfma(ux2, uy2, CS2 * (ux2 + uy2))));
+    V r[9];
     central_to_raw_sep(k, ux, uy, r);
     // The raw first moments of the post-collision state are exactly
     // rho cs2 u + cs2 F_t / 2 = j + cs2 F_t (j: pre-collision momentum, with
@@ -514,9 +582,8 @@ __device__ __forceinline__ void collide_flow(float a[9], const FlowMacro& m, flo
     // forward without passing through the rounded u: re-forming it from u
     // every step adds the rounding of u to the momentum, and for a slowly
     // varying flow that rounding repeats step after step and accumulates.
-    // Explicit FMAs: every kernel that inlines this rounds it the same way.
-    r[1] = __fmaf_rn(CS2, m.Ftx, jx);
-    r[2] = __fmaf_rn(CS2, m.Fty, jy);
+    r[1] = vfma(CS2, m.Ftx, jx);
+    r[2] = vfma(CS2, m.Fty, jy);
     raw_to_pops(r, a, out_scale);
 }
 
@@ -524,17 +591,18 @@ __device__ __forceinline__ void collide_flow(float a[9], const FlowMacro& m, flo
 // is only read back by the bounce-back of the same cell (App. D set-up,
 // half-way bounce-back): slot q at the bottom row (e_qy = -1) feeds direction
 // opp(q) with u_w = (-u_wall, 0); at the top row (e_qy = +1) u_w = (+u_wall, 0).
-__device__ __forceinline__ void wall_correct_flow(float a[9], const KParams& p, int j, float rho,
+template <class V>
+__device__ __forceinline__ void wall_correct_flow(V a[9], const KParams& p, int j, V rho,
                                                   float out_scale = 1.0f) {
     if (!p.walls) return;
     if (j == 0) {
         // 2 w_opp rho (e_opp . u_w), u_w = -u_wall: opp(4)=2 (0), opp(7)=5 (+1), opp(8)=6 (-1)
-        const float t = 2.0f * (1.0f / 36.0f) * rho * (-p.u_wall) * out_scale;
+        const V t = (2.0f * (1.0f / 36.0f) * (-p.u_wall) * out_scale) * rho;
         a[7] += t;   // e_5x = +1
         a[8] -= t;   // e_6x = -1
     }
     if (j == p.ny - 1) {
-        const float t = 2.0f * (1.0f / 36.0f) * rho * (p.u_wall) * out_scale;
+        const V t = (2.0f * (1.0f / 36.0f) * (p.u_wall) * out_scale) * rho;
         a[5] -= t;   // opp(5) = 7, e_7x = -1
         a[6] += t;   // opp(6) = 8, e_8x = +1
     }

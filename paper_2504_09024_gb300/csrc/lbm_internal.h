@@ -21,20 +21,42 @@ struct DevState {
     int nlat;               // 2 (fixed velocity) or 3 (coupled)
 };
 
+// Store modes of the bulk-tensor sweep (lbm_sweep2.cuh): direct stores from
+// registers, or staged rows written by bulk-tensor stores.
+constexpr int OUT_DIRECT = 0;
+constexpr int OUT_STAGED = 1;
+
 // Fused-kernel launch shape.
 struct FusedShape {
-    int bx;    // threads per block = interior columns + 4
-    int seg;   // rows per block
+    int bx;       // columns per block (interior columns + 4)
+    int seg;      // rows per block
+    int cpt = 1;  // cells (adjacent columns) per thread of the bulk-tensor sweep
+    int out = 0;  // its store mode: 0 direct stores, 1 staged bulk-tensor stores
 };
 
-// One run of a batch, as the batched step kernel sees it.
+// Bulk-tensor store maps of one population buffer (bulk-tensor sweep): the
+// scalar lattices' word planes and the flow lattice's, boxes {own columns,
+// 1 row, planes}, over the columns -4 .. nx-1 of each row.
+struct StoreMaps {
+    CUtensorMap s, f;
+};
+
+// One run of a batch, as the persistent batch kernel sees it (global memory).
 struct alignas(128) RunDesc {
-    CUtensorMap tmap[2];    // bulk-tensor maps over the run's two population buffers
-    KParams p;
-    float* pop[2];
+    CUtensorMap tmap[2];    // bulk-tensor load maps over the run's two population buffers
+    StoreMaps smap[2];      // bulk-tensor store maps over the same buffers
+    float* pop[2];          // column 0 of each buffer
     float* fields;
     int seg;                // rows per tile
     int flip;               // the run reads buffer (parity ^ flip) at batch parity `parity`
+};
+
+// Parameters of up to BATCH_TABLE_RUNS runs, passed to the persistent batch
+// kernel as one kernel parameter (read through the constant cache); larger
+// batches take one launch per table per step.
+constexpr int BATCH_TABLE_RUNS = 64;
+struct BatchTable {
+    KParams p[BATCH_TABLE_RUNS];
 };
 
 // Launchers (all asynchronous on `st`).
@@ -42,30 +64,45 @@ void launch_step_split(const KParams& p, const DevState& s, int src, cudaStream_
 void launch_step_fused(const KParams& p, const DevState& s, int src, const FusedShape& sh,
                        cudaStream_t st);
 size_t fused_smem_bytes(int bx);
-// Fused step with bulk-tensor staging (lbm_sweep_tma.cu).
+// Bulk-tensor load map over one population buffer: dims {pitch, ny, planes},
+// box {bx + 4, 1, planes} (lbm_sweep_tma.cu).
 bool tma_available();
 bool make_tensor_map(CUtensorMap* map, float* alloc, const KParams& p, int nplanes, int bx);
-size_t tma_smem_bytes(int bx, bool coupled);
-cudaError_t configure_tma_smem();
-void launch_step_tma(const KParams& p, const DevState& s, int src, const FusedShape& sh,
-                     const CUtensorMap* maps, int* err, cudaStream_t st);
-// Batched step: one persistent launch over `nitems` tiles (int4: run, strip,
-// segment, unused) of runs sharing block width bx and lattice count.
-void launch_step_tma_batch(const RunDesc* runs, const int4* items, int nitems, int blocks,
-                           int bx, bool coupled, int src, int* err, cudaStream_t st);
-int tma_batch_blocks_per_sm(int bx, bool coupled);
-int tma_blocks_per_sm(int bx, bool coupled);
-// Fused TMA step with 16-bit storage (lbm_sweep_tma16.cu; block width 128 or 192).
-// st: ST_F16 or ST_BF16 (lbm_store16.cuh); buffers hold store_planes(st, .)
-// word planes, pointers to column 0 like the FP32 ones.
-size_t tma16_smem_bytes(int bx, bool coupled);
-cudaError_t configure_tma16_smem();
-int tma16_blocks_per_sm(int bx, bool coupled, int st);
-void launch_step_tma16(const KParams& p, float* src16, float* dst16, const float* fields,
-                       const FusedShape& sh, const CUtensorMap& map, int st, int* err,
+// Bulk-tensor sweep with staged stores and cells per thread (lbm_sweep2.cuh):
+// FP32 kernels in lbm_sweep_tma.cu, 16-bit ones in lbm_sweep_tma16.cu.
+bool sweep2_shape_ok(int bx, int cpt, int st);
+size_t sweep2_smem_bytes(int bx, int cpt, int out, bool coupled, int st);
+int sweep2_blocks_per_sm(int bx, int cpt, int out, bool coupled, int st);
+cudaError_t configure_sweep2_smem();
+bool make_store_maps(StoreMaps* m, float* alloc, const KParams& p, int st, int bx);
+void launch_step_sweep2(const KParams& p, float* dst, const float* fields, const FusedShape& sh,
+                        const CUtensorMap& load_map, const StoreMaps& store_maps, int st,
+                        int* err, cudaStream_t s);
+// (per storage format)
+bool sweep2_f32_shape_ok(int bx, int cpt);
+size_t sweep2_f32_smem_bytes(int bx, int cpt, int out, bool coupled);
+int sweep2_f32_blocks_per_sm(int bx, int cpt, int out, bool coupled);
+cudaError_t configure_sweep2_f32_smem();
+void launch_sweep2_f32(const KParams& p, float* dst, const float* fields, const FusedShape& sh,
+                       const CUtensorMap& load_map, const StoreMaps& store_maps, int* err,
                        cudaStream_t s);
-// Advance the device step counter of the stochastic rounding by n.
+bool sweep2_16_shape_ok(int bx, int cpt);
+size_t sweep2_16_smem_bytes(int bx, int cpt, bool coupled);
+int sweep2_16_blocks_per_sm(int bx, int cpt, bool coupled, int st);
+cudaError_t configure_sweep2_16_smem();
+void launch_sweep2_16(const KParams& p, float* dst, const float* fields, const FusedShape& sh,
+                      const CUtensorMap& load_map, const StoreMaps& store_maps, int st, int* err,
+                      cudaStream_t s);
+// Batched step: one persistent launch over `nitems` tiles (int4: entry of
+// tab, strip, segment, run) of runs sharing the launch shape (FP32 storage).
+void launch_sweep2_batch(const BatchTable& tab, const RunDesc* runs, const int4* items,
+                         int nitems, int blocks, const FusedShape& sh, bool coupled, int parity,
+                         int* err, cudaStream_t st);
+int sweep2_batch_blocks_per_sm(int bx, int cpt, int out, bool coupled);
+// Advance the device step counter of the stochastic roundings by n (one
+// counter, or the counters of nctr runs).
 void launch_step_advance(unsigned* ctr, unsigned n, cudaStream_t s);
+void launch_step_advance_many(unsigned* const* ctrs, int nctr, unsigned n, cudaStream_t s);
 // Whole-buffer conversions between the FP32 deviation-form layout and the
 // 16-bit layout (allocation base pointers; ghost columns included).
 void launch_pack16(const KParams& p, const float* src32_alloc, float* dst16_alloc, int st,

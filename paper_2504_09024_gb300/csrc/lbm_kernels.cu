@@ -27,10 +27,11 @@ __global__ void k_fields(KParams p, const float* __restrict__ src, float* __rest
     const int j = blockIdx.y;
     if (i >= p.nx) return;
     const int64_t idx = (int64_t)j * p.pitch + i;
+    const uint32_t bits = moment_bits(step_seed(p), i, j, p.nx);
     ScalarMoments m = pull_scalar(src, p, 0, i, j);
-    F[FP_PHI * p.plane + idx] = __int_as_float(fx_add(m.s0, m.inc, p.fx_scale[0]));
+    F[FP_PHI * p.plane + idx] = __int_as_float(fx_add_sr(m.s0, m.inc, p.fx_scale[0], bits));
     m = pull_scalar(src + 9 * p.plane, p, 1, i, j);
-    const int c_fx = fx_add(m.s0, m.inc, p.fx_scale[1]);
+    const int c_fx = fx_add_sr(m.s0, m.inc, p.fx_scale[1], second_bits(bits));
     F[FP_C * p.plane + idx] = __int_as_float(c_fx);
     F[FP_SIG * p.plane + idx] = sigma_of_c(p, (float)c_fx * p.fx_inv[1]);
     if (COUPLED) {
@@ -101,8 +102,9 @@ __global__ void k_collide(KParams p, const float* __restrict__ src, float* __res
     CellGeom g = gather_geom<COUPLED>(p, F, i, j);
     const ScalarMoments mf = pull_scalar(src, p, 0, i, j);
     const ScalarMoments mh = pull_scalar(src + 9 * p.plane, p, 1, i, j);
-    const int f_fx = fx_add(mf.s0, mf.inc, p.fx_scale[0]);
-    const int h_fx = fx_add(mh.s0, mh.inc, p.fx_scale[1]);
+    const uint32_t bits = moment_bits(step_seed(p), i, j, p.nx);
+    const int f_fx = fx_add_sr(mf.s0, mf.inc, p.fx_scale[0], bits);
+    const int h_fx = fx_add_sr(mh.s0, mh.inc, p.fx_scale[1], second_bits(bits));
     float gg[9], df[9], dh[9];
     float ufx = 0.0f, ufy = 0.0f;
     if (COUPLED) {
@@ -190,6 +192,7 @@ __global__ void __launch_bounds__(128) k_fused_sweep(KParams p, const float* __r
     else if (col == x0 - 1 || col == xend) role = 2;
     else if (col == x0 - 2 || col == xend + 1) role = 1;
     const int i = wrap_i(col, p.nx);
+    const uint32_t seed = step_seed(p);
 
     for (int r = y0 - 2; r <= y1 + 1; ++r) {
         // A: stream row r and form its moments
@@ -198,15 +201,16 @@ __global__ void __launch_bounds__(128) k_fused_sweep(KParams p, const float* __r
             const int jj = ext_row(r, p.ny, p.walls);
             const bool keep = role == 3 && r >= y0 && r < y1;
             float* pp = s_pop + ((r + 3 * PRING) % PRING) * PSLOT * bx;
+            const uint32_t bits = moment_bits(seed, i, jj, p.nx);
             ScalarMoments m = pull_scalar(src, p, 0, i, jj);
-            s_phi[slot * bx + t] = fx_add(m.s0, m.inc, p.fx_scale[0]);
+            s_phi[slot * bx + t] = fx_add_sr(m.s0, m.inc, p.fx_scale[0], bits);
             if (keep) {
                 pp[0 * bx + t] = m.jx;
                 pp[1 * bx + t] = m.jy;
             }
             if (role >= 2 && r >= y0 - 1 && r <= y1) {
                 m = pull_scalar(src + 9 * p.plane, p, 1, i, jj);
-                const int c_fx = fx_add(m.s0, m.inc, p.fx_scale[1]);
+                const int c_fx = fx_add_sr(m.s0, m.inc, p.fx_scale[1], second_bits(bits));
                 const float c = (float)c_fx * p.fx_inv[1];
                 s_c[slot * bx + t] = c;
                 s_sig[slot * bx + t] = sigma_of_c(p, c);

@@ -64,18 +64,9 @@ __device__ __forceinline__ uint32_t pack2(float a, float b) {
 // Stochastic rounding of the stored deviations.  Round-to-nearest makes the
 // rounding error of a slowly varying deviation the same every step, and the
 // zeroth moments integrate it; rounding up with probability equal to the
-// dropped fraction makes it zero-mean.  The random bits come from a
-// counter-based hash of (step, cell): the PCG hash of Jarzynski and Olano,
-// "Hash Functions for GPU Rendering", JCGT 9(3), 2020 (the output
-// permutation of the PCG generator, O'Neill 2014, applied to one LCG step of
-// the input), one hash per cell and warp group, spread over the words of the
-// cell by word_bits.
-__device__ __forceinline__ uint32_t pcg_hash(uint32_t v) {
-    const uint32_t state = v * 747796405u + 2891336453u;
-    const uint32_t word = ((state >> ((state >> 28u) + 4u)) ^ state) * 277803737u;
-    return (word >> 22u) ^ word;
-}
-
+// dropped fraction makes it zero-mean.  The random bits come from the
+// counter-based hash pcg_hash of (step, cell) (lbm_device.cuh), one hash per
+// cell and warp group, spread over the words of the cell by word_bits.
 // Random bits of word k of a cell from the cell's hash h: the product with a
 // distinct odd constant per word is a bijection of the low bits (uniform if
 // h is), which is all the rounding of one word needs.

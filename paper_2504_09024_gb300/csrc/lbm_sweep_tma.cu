@@ -1,62 +1,49 @@
-// Fused step with bulk-tensor (TMA) staging, FP32 populations: the step
-// kernels (single run and batched), tensor maps and launchers.  The sweep of
-// one tile is in lbm_sweep_tile.cuh.
+// Fused step with bulk-tensor (TMA) loads and stores, FP32 populations: the
+// step kernels (single run, and the persistent kernel over the tiles of a
+// batch of runs), tensor maps and launchers.  The sweep of one tile is in
+// lbm_sweep2.cuh.
 #include <cstdio>
+#include <cstring>
 #include <type_traits>
 
 #include <cudaTypedefs.h>
 
-#include "lbm_sweep_tile.cuh"
+#include "lbm_sweep2.cuh"
 
 namespace lbm {
 
-template <int BX, bool COUPLED>
-__global__ void __launch_bounds__(2 * BX, tma_min_blocks<BX>()) k_sweep_tma(const __grid_constant__ CUtensorMap tmap,
-                                                  KParams p, float* __restrict__ dst,
-                                                  const float* __restrict__ F, int seg,
-                                                  int* __restrict__ err) {
-    extern __shared__ unsigned char smem_raw[];
-    const TmaSmem<BX, COUPLED, ST_F32> S(smem_raw);
+// One time step of every run of a batch in one launch: each block walks the
+// flat tile list with a stride of the grid size.  Runs may differ in size and
+// parameters; run r's parameters are tab.p[r] (a kernel parameter, so they
+// are read through the constant cache), its buffers and tensor maps are in
+// runs[] (global memory).
+template <int BX, int CPT, bool COUPLED, int OUT>
+__global__ void __launch_bounds__(2 * BX / CPT, (sweep2_min_blocks<BX, CPT, COUPLED, ST_F32, OUT>()))
+    k_sweep2_batch(const __grid_constant__ BatchTable tab, const RunDesc* __restrict__ runs,
+                   const int4* __restrict__ items, int nitems, int parity,
+                   int* __restrict__ err) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    // the bulk-tensor copies need the carve-up on 128-byte boundaries
+    if (smem_u32(smem_raw) & 127u) {
+        if (threadIdx.x == 0) atomicExch(err, 2);
+        return;
+    }
+    const SweepSmem<BX, CPT, COUPLED, ST_F32, OUT> S(smem_raw);
     if (threadIdx.x == 0) {
-        for (int k = 0; k <= TMA_STAGES; ++k) mbar_init(&S.bars[k], 1);  // [TMA_STAGES]: test hook
+        // [STAGES]: the failure-path test hook
+        for (int k = 0; k <= sw_stages(ST_F32, OUT); ++k) mbar_init(&S.bars[k], 1);
         fence_barrier_init();
     }
     __syncthreads();
-    uint32_t issued = 0;
-    sweep_tile<BX, COUPLED, ST_F32>(&tmap, p, dst, F, seg, blockIdx.x, blockIdx.y, S, issued, err);
-}
-
-// Batched step: every block walks the flat tile list with a stride of the
-// grid size; runs may differ in size and parameters.
-template <int BX, bool COUPLED>
-__global__ void __launch_bounds__(2 * BX, tma_min_blocks<BX>()) k_sweep_tma_batch(const RunDesc* __restrict__ runs,
-                                                        const int4* __restrict__ items, int nitems,
-                                                        int parity, int* __restrict__ err) {
-    extern __shared__ unsigned char smem_raw[];
-    const TmaSmem<BX, COUPLED, ST_F32> S(smem_raw);
-    if (threadIdx.x == 0) {
-        for (int k = 0; k <= TMA_STAGES; ++k) mbar_init(&S.bars[k], 1);
-        fence_barrier_init();
-    }
-    __syncthreads();
-    // the run's parameters are read from shared memory, not held in registers
-    __shared__ KParams sp;
     uint32_t issued = 0;
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
-        const int4 w = items[it];
-        const RunDesc* rd = runs + w.x;
-        {
-            const int* srcw = reinterpret_cast<const int*>(&rd->p);
-            int* dstw = reinterpret_cast<int*>(&sp);
-            for (int k = threadIdx.x; k < (int)(sizeof(KParams) / sizeof(int)); k += blockDim.x)
-                dstw[k] = srcw[k];
-        }
-        __syncthreads();
+        const int4 w = items[it];  // (entry of tab, strip, segment, run)
+        const RunDesc* rd = runs + w.w;
         const int src = parity ^ rd->flip;
-        const bool ok = sweep_tile<BX, COUPLED, ST_F32>(&rd->tmap[src], sp, rd->pop[1 - src],
-                                                rd->fields, rd->seg, w.y, w.z, S, issued, err);
+        const bool ok = sweep_tile2<BX, CPT, COUPLED, ST_F32, OUT>(
+            &rd->tmap[src], &rd->smap[1 - src], tab.p[w.x], rd->pop[1 - src], rd->fields, rd->seg,
+            w.y, w.z, S, issued, err);
         if (!ok) break;
-        __syncthreads();  // the next tile reuses the shared rings and parameters
     }
 }
 
@@ -79,12 +66,6 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-template <int BX, bool COUPLED>
-void set_attr() {
-    cudaFuncSetAttribute(k_sweep_tma<BX, COUPLED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)TmaLayout<BX, COUPLED, ST_F32>::bytes);
-}
-
 }  // namespace
 
 bool tma_available() { return encode_fn() != nullptr; }
@@ -105,91 +86,176 @@ bool make_tensor_map(CUtensorMap* map, float* alloc, const KParams& p, int nplan
     return r == CUDA_SUCCESS;
 }
 
+// ---------------------------------------------------------------------------
+// bulk-tensor sweep, FP32 storage: shapes, shared memory, launch
+// ---------------------------------------------------------------------------
+
 namespace {
 
-// Calls f with the block width as a compile-time constant (64, 128 or 192).
+// Calls f with (block width, cells per thread, store mode) as compile-time
+// constants for the FP32 shapes: (64, 1), (128, 1), (192, 1), (128, 2),
+// (192, 2), each with direct or staged stores.
 template <typename F>
-auto with_bx(int bx, F&& f) {
-    if (bx == 192) return f(std::integral_constant<int, 192>{});
-    if (bx == 64) return f(std::integral_constant<int, 64>{});
-    return f(std::integral_constant<int, 128>{});
-}
-
-bool bx_supported(int bx) { return bx == 64 || bx == 128 || bx == 192; }
-
-template <int BX, bool COUPLED>
-void set_attr_batch() {
-    cudaFuncSetAttribute(k_sweep_tma_batch<BX, COUPLED>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)TmaLayout<BX, COUPLED, ST_F32>::bytes);
+auto with_shape_f32(int bx, int cpt, int out, F&& f) {
+    using std::integral_constant;
+    auto go = [&](auto B, auto C) {
+        return out == OUT_STAGED ? f(B, C, integral_constant<int, OUT_STAGED>{})
+                                 : f(B, C, integral_constant<int, OUT_DIRECT>{});
+    };
+    if (cpt == 2)
+        return bx == 192 ? go(integral_constant<int, 192>{}, integral_constant<int, 2>{})
+                         : go(integral_constant<int, 128>{}, integral_constant<int, 2>{});
+    if (bx == 192) return go(integral_constant<int, 192>{}, integral_constant<int, 1>{});
+    if (bx == 64) return go(integral_constant<int, 64>{}, integral_constant<int, 1>{});
+    return go(integral_constant<int, 128>{}, integral_constant<int, 1>{});
 }
 
 }  // namespace
 
-size_t tma_smem_bytes(int bx, bool coupled) {
-    if (!bx_supported(bx)) return 0;
-    return with_bx(bx, [&](auto B) -> size_t {
-        return coupled ? TmaLayout<B(), true, ST_F32>::bytes : TmaLayout<B(), false, ST_F32>::bytes;
+bool sweep2_f32_shape_ok(int bx, int cpt) {
+    return (cpt == 1 && (bx == 64 || bx == 128 || bx == 192)) ||
+           (cpt == 2 && (bx == 128 || bx == 192));
+}
+
+size_t sweep2_f32_smem_bytes(int bx, int cpt, int out, bool coupled) {
+    if (!sweep2_f32_shape_ok(bx, cpt)) return 0;
+    return with_shape_f32(bx, cpt, out, [&](auto B, auto C, auto O) -> size_t {
+        return coupled ? SweepLayout<B(), C(), true, ST_F32, O()>::bytes
+                       : SweepLayout<B(), C(), false, ST_F32, O()>::bytes;
     });
 }
 
-cudaError_t configure_tma_smem() {
-    for (int bx : {64, 128, 192})
-        with_bx(bx, [](auto B) {
-            set_attr<B(), true>();
-            set_attr<B(), false>();
-            set_attr_batch<B(), true>();
-            set_attr_batch<B(), false>();
-            return 0;
-        });
+cudaError_t configure_sweep2_f32_smem() {
+    const int shapes[5][2] = {{64, 1}, {128, 1}, {192, 1}, {128, 2}, {192, 2}};
+    for (const auto& sh : shapes)
+        for (int out : {OUT_DIRECT, OUT_STAGED})
+            with_shape_f32(sh[0], sh[1], out, [](auto B, auto C, auto O) {
+                const int bt = (int)SweepLayout<B(), C(), true, ST_F32, O()>::bytes;
+                const int bf = (int)SweepLayout<B(), C(), false, ST_F32, O()>::bytes;
+                cudaFuncSetAttribute(k_sweep2<B(), C(), true, ST_F32, O()>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, bt);
+                cudaFuncSetAttribute(k_sweep2<B(), C(), false, ST_F32, O()>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, bf);
+                cudaFuncSetAttribute(k_sweep2_batch<B(), C(), true, O()>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, bt);
+                cudaFuncSetAttribute(k_sweep2_batch<B(), C(), false, O()>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, bf);
+                return 0;
+            });
     return cudaGetLastError();
 }
 
-int tma_batch_blocks_per_sm(int bx, bool coupled) {
+int sweep2_f32_blocks_per_sm(int bx, int cpt, int out, bool coupled) {
     int n = 0;
-    const size_t smem = tma_smem_bytes(bx, coupled);
-    const cudaError_t e = with_bx(bx, [&](auto B) {
-        return coupled ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep_tma_batch<B(), true>, 2 * B(), smem)
-                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep_tma_batch<B(), false>, 2 * B(), smem);
+    const size_t smem = sweep2_f32_smem_bytes(bx, cpt, out, coupled);
+    const cudaError_t e = with_shape_f32(bx, cpt, out, [&](auto B, auto C, auto O) {
+        return coupled ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                             &n, k_sweep2<B(), C(), true, ST_F32, O()>, 2 * B() / C(), smem)
+                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                             &n, k_sweep2<B(), C(), false, ST_F32, O()>, 2 * B() / C(), smem);
     });
     return e == cudaSuccess && n > 0 ? n : 1;
 }
 
-int tma_blocks_per_sm(int bx, bool coupled) {
-    int n = 0;
-    const size_t smem = tma_smem_bytes(bx, coupled);
-    const cudaError_t e = with_bx(bx, [&](auto B) {
-        return coupled ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep_tma<B(), true>, 2 * B(), smem)
-                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep_tma<B(), false>, 2 * B(), smem);
-    });
-    return e == cudaSuccess && n > 0 ? n : 1;
-}
-
-void launch_step_tma_batch(const RunDesc* runs, const int4* items, int nitems, int blocks,
-                           int bx, bool coupled, int src, int* err, cudaStream_t st) {
-    const size_t smem = tma_smem_bytes(bx, coupled);
-    with_bx(bx, [&](auto B) {
-        if (coupled)
-            k_sweep_tma_batch<B(), true><<<blocks, 2 * B(), smem, st>>>(runs, items, nitems, src, err);
-        else
-            k_sweep_tma_batch<B(), false><<<blocks, 2 * B(), smem, st>>>(runs, items, nitems, src, err);
-        return 0;
-    });
-}
-
-void launch_step_tma(const KParams& p, const DevState& s, int src, const FusedShape& sh,
-                     const CUtensorMap* maps, int* err, cudaStream_t st) {
+void launch_sweep2_f32(const KParams& p, float* dst, const float* fields, const FusedShape& sh,
+                       const CUtensorMap& load_map, const StoreMaps& store_maps, int* err,
+                       cudaStream_t s) {
     const int tx = sh.bx - 4;
     dim3 grid((p.nx + tx - 1) / tx, (p.ny + sh.seg - 1) / sh.seg);
-    const size_t smem = tma_smem_bytes(sh.bx, p.coupled);
-    float* dst = s.pop[1 - src];
-    with_bx(sh.bx, [&](auto B) {
+    const size_t smem = sweep2_f32_smem_bytes(sh.bx, sh.cpt, sh.out, p.coupled);
+    with_shape_f32(sh.bx, sh.cpt, sh.out, [&](auto B, auto C, auto O) {
         if (p.coupled)
-            k_sweep_tma<B(), true><<<grid, 2 * B(), smem, st>>>(maps[src], p, dst, s.fields, sh.seg, err);
+            k_sweep2<B(), C(), true, ST_F32, O()><<<grid, 2 * B() / C(), smem, s>>>(
+                load_map, store_maps, p, dst, fields, sh.seg, err);
         else
-            k_sweep_tma<B(), false><<<grid, 2 * B(), smem, st>>>(maps[src], p, dst, s.fields, sh.seg, err);
+            k_sweep2<B(), C(), false, ST_F32, O()><<<grid, 2 * B() / C(), smem, s>>>(
+                load_map, store_maps, p, dst, fields, sh.seg, err);
         return 0;
     });
+}
+
+int sweep2_batch_blocks_per_sm(int bx, int cpt, int out, bool coupled) {
+    int n = 0;
+    const size_t smem = sweep2_f32_smem_bytes(bx, cpt, out, coupled);
+    const cudaError_t e = with_shape_f32(bx, cpt, out, [&](auto B, auto C, auto O) {
+        return coupled ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                             &n, k_sweep2_batch<B(), C(), true, O()>, 2 * B() / C(), smem)
+                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                             &n, k_sweep2_batch<B(), C(), false, O()>, 2 * B() / C(), smem);
+    });
+    return e == cudaSuccess && n > 0 ? n : 1;
+}
+
+void launch_sweep2_batch(const BatchTable& tab, const RunDesc* runs, const int4* items,
+                         int nitems, int blocks, const FusedShape& sh, bool coupled, int parity,
+                         int* err, cudaStream_t st) {
+    const size_t smem = sweep2_f32_smem_bytes(sh.bx, sh.cpt, sh.out, coupled);
+    with_shape_f32(sh.bx, sh.cpt, sh.out, [&](auto B, auto C, auto O) {
+        if (coupled)
+            k_sweep2_batch<B(), C(), true, O()><<<blocks, 2 * B() / C(), smem, st>>>(
+                tab, runs, items, nitems, parity, err);
+        else
+            k_sweep2_batch<B(), C(), false, O()><<<blocks, 2 * B() / C(), smem, st>>>(
+                tab, runs, items, nitems, parity, err);
+        return 0;
+    });
+}
+
+// Store maps over one buffer: dims {4 + nx rounded down to a multiple of 4
+// (columns -4 .. that end), ny, planes}, boxes {bx - 4, 1, scalar planes} and
+// {bx - 4, 1, flow planes}.  The column extent ends on a 16-byte boundary: a
+// store box clipped elsewhere was seen to write past the extent (into the
+// ghost columns), so the sweep stores the last nx mod 4 columns directly.
+bool make_store_maps(StoreMaps* m, float* alloc, const KParams& p, int st, int bx) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+    if (!enc) return false;
+    const int nplanes = store_planes(st, p.coupled);
+    const int ns = st == ST_F32 ? 18 : 10;
+    const int nf = nplanes - ns;
+    cuuint64_t dims[3] = {(cuuint64_t)(XGHOST + (p.nx & ~3)), (cuuint64_t)p.ny,
+                          (cuuint64_t)nplanes};
+    cuuint64_t strides[2] = {(cuuint64_t)p.pitch * sizeof(float),
+                             (cuuint64_t)p.plane * sizeof(float)};
+    cuuint32_t estr[3] = {1u, 1u, 1u};
+    auto encode = [&](CUtensorMap* map, int planes) {
+        cuuint32_t box[3] = {(cuuint32_t)(bx - 4), 1u, (cuuint32_t)planes};
+        return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, alloc, dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                   CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+               CUDA_SUCCESS;
+    };
+    std::memset(m, 0, sizeof(StoreMaps));
+    if (!encode(&m->s, ns)) return false;
+    return nf == 0 || encode(&m->f, nf);
+}
+
+bool sweep2_shape_ok(int bx, int cpt, int st) {
+    return st == ST_F32 ? sweep2_f32_shape_ok(bx, cpt) : sweep2_16_shape_ok(bx, cpt);
+}
+
+size_t sweep2_smem_bytes(int bx, int cpt, int out, bool coupled, int st) {
+    return st == ST_F32 ? sweep2_f32_smem_bytes(bx, cpt, out, coupled)
+                        : sweep2_16_smem_bytes(bx, cpt, coupled);
+}
+
+int sweep2_blocks_per_sm(int bx, int cpt, int out, bool coupled, int st) {
+    return st == ST_F32 ? sweep2_f32_blocks_per_sm(bx, cpt, out, coupled)
+                        : sweep2_16_blocks_per_sm(bx, cpt, coupled, st);
+}
+
+cudaError_t configure_sweep2_smem() {
+    cudaError_t e = configure_sweep2_f32_smem();
+    if (e != cudaSuccess) return e;
+    return configure_sweep2_16_smem();
+}
+
+void launch_step_sweep2(const KParams& p, float* dst, const float* fields, const FusedShape& sh,
+                        const CUtensorMap& load_map, const StoreMaps& store_maps, int st,
+                        int* err, cudaStream_t s) {
+    if (st == ST_F32)
+        launch_sweep2_f32(p, dst, fields, sh, load_map, store_maps, err, s);
+    else
+        launch_sweep2_16(p, dst, fields, sh, load_map, store_maps, st, err, s);
 }
 
 }  // namespace lbm

@@ -3,31 +3,16 @@
 // FP32 deviation-form state that initialisation and field output use.
 //
 // The word-plane layout is described in lbm_store16.cuh.  The per-cell
-// arithmetic of the step is the FP32 step's (lbm_sweep_tile.cuh): only the
-// pull (unpack, unscale) and the store (scale, round stochastically, pack)
+// arithmetic of the step is the FP32 step's (lbm_sweep2.cuh): only the pull
+// (unpack, unscale) and the store (scale, round stochastically, pack)
 // differ.  Whole-buffer packing (initialisation, set_populations) rounds to
 // nearest.
 #include <cudaTypedefs.h>
 #include <type_traits>
 
-#include "lbm_sweep_tile.cuh"
+#include "lbm_sweep2.cuh"
 
 namespace lbm {
-
-template <int BX, bool COUPLED, int ST>
-__global__ void __launch_bounds__(2 * BX, tma_min_blocks<BX>()) k_sweep_tma16(
-    const __grid_constant__ CUtensorMap tmap, KParams p, float* __restrict__ dst,
-    const float* __restrict__ F, int seg, int* __restrict__ err) {
-    extern __shared__ unsigned char smem_raw[];
-    const TmaSmem<BX, COUPLED, ST> S(smem_raw);
-    if (threadIdx.x == 0) {
-        for (int k = 0; k <= TMA_STAGES; ++k) mbar_init(&S.bars[k], 1);  // [TMA_STAGES]: test hook
-        fence_barrier_init();
-    }
-    __syncthreads();
-    uint32_t issued = 0;
-    sweep_tile<BX, COUPLED, ST>(&tmap, p, dst, F, seg, blockIdx.x, blockIdx.y, S, issued, err);
-}
 
 // FP32 deviation-form buffer (27 or 18 float planes) -> 16-bit words (15 or
 // 10 planes), element by element over whole planes (ghost columns included).
@@ -79,74 +64,100 @@ __global__ void k_unpack16(const float* __restrict__ src, float* __restrict__ ds
 
 __global__ void k_step_advance(unsigned* ctr, unsigned n) { *ctr += n; }
 
+__global__ void k_step_advance_many(unsigned* const* ctrs, int nctr, unsigned n) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < nctr) *ctrs[k] += n;
+}
+
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
 
+// ---------------------------------------------------------------------------
+// bulk-tensor sweep, 16-bit storage: shapes (128 or 192 columns, 1 or 2 cells
+// per thread), shared memory, launch
+// ---------------------------------------------------------------------------
+
 namespace {
 
-// Calls f with the block width (128 or 192) and the storage format as
-// compile-time constants.
 template <typename F>
-auto with_bx_st(int bx, int st, F&& f) {
-    if (bx == 192)
-        return st == ST_F16 ? f(std::integral_constant<int, 192>{}, std::integral_constant<int, ST_F16>{})
-                            : f(std::integral_constant<int, 192>{}, std::integral_constant<int, ST_BF16>{});
-    return st == ST_F16 ? f(std::integral_constant<int, 128>{}, std::integral_constant<int, ST_F16>{})
-                        : f(std::integral_constant<int, 128>{}, std::integral_constant<int, ST_BF16>{});
+auto with_shape16(int bx, int cpt, int st, F&& f) {
+    using std::integral_constant;
+    auto go = [&](auto B, auto C) {
+        return st == ST_F16 ? f(B, C, integral_constant<int, ST_F16>{})
+                            : f(B, C, integral_constant<int, ST_BF16>{});
+    };
+    if (cpt == 2)
+        return bx == 192 ? go(integral_constant<int, 192>{}, integral_constant<int, 2>{})
+                         : go(integral_constant<int, 128>{}, integral_constant<int, 2>{});
+    return bx == 192 ? go(integral_constant<int, 192>{}, integral_constant<int, 1>{})
+                     : go(integral_constant<int, 128>{}, integral_constant<int, 1>{});
 }
 
 }  // namespace
 
-size_t tma16_smem_bytes(int bx, bool coupled) {
-    if (bx != 128 && bx != 192) return 0;
+bool sweep2_16_shape_ok(int bx, int cpt) { return (bx == 128 || bx == 192) && (cpt == 1 || cpt == 2); }
+
+size_t sweep2_16_smem_bytes(int bx, int cpt, bool coupled) {
+    if (!sweep2_16_shape_ok(bx, cpt)) return 0;
     // FP16 and BF16 words have the same layout
-    return with_bx_st(bx, ST_F16, [&](auto B, auto) -> size_t {
-        return coupled ? TmaLayout<B(), true, ST_F16>::bytes : TmaLayout<B(), false, ST_F16>::bytes;
+    return with_shape16(bx, cpt, ST_F16, [&](auto B, auto C, auto) -> size_t {
+        return coupled ? SweepLayout<B(), C(), true, ST_F16, OUT_STAGED>::bytes
+                       : SweepLayout<B(), C(), false, ST_F16, OUT_STAGED>::bytes;
     });
 }
 
-cudaError_t configure_tma16_smem() {
+cudaError_t configure_sweep2_16_smem() {
     for (int bx : {128, 192})
-        for (int st : {ST_F16, ST_BF16})
-            with_bx_st(bx, st, [&](auto B, auto S) {
-                cudaFuncSetAttribute(k_sweep_tma16<B(), true, S()>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)tma16_smem_bytes(B(), true));
-                cudaFuncSetAttribute(k_sweep_tma16<B(), false, S()>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)tma16_smem_bytes(B(), false));
-                return 0;
-            });
+        for (int cpt : {1, 2})
+            for (int st : {ST_F16, ST_BF16})
+                with_shape16(bx, cpt, st, [&](auto B, auto C, auto S) {
+                    cudaFuncSetAttribute(k_sweep2<B(), C(), true, S(), OUT_STAGED>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)SweepLayout<B(), C(), true, S(), OUT_STAGED>::bytes);
+                    cudaFuncSetAttribute(k_sweep2<B(), C(), false, S(), OUT_STAGED>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)SweepLayout<B(), C(), false, S(), OUT_STAGED>::bytes);
+                    return 0;
+                });
     return cudaGetLastError();
 }
 
-int tma16_blocks_per_sm(int bx, bool coupled, int st) {
+int sweep2_16_blocks_per_sm(int bx, int cpt, bool coupled, int st) {
     int n = 0;
-    const size_t smem = tma16_smem_bytes(bx, coupled);
-    const cudaError_t e = with_bx_st(bx, st, [&](auto B, auto S) {
-        return coupled ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep_tma16<B(), true, S()>, 2 * B(), smem)
-                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep_tma16<B(), false, S()>, 2 * B(), smem);
+    const size_t smem = sweep2_16_smem_bytes(bx, cpt, coupled);
+    const cudaError_t e = with_shape16(bx, cpt, st, [&](auto B, auto C, auto S) {
+        return coupled ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                             &n, k_sweep2<B(), C(), true, S(), OUT_STAGED>, 2 * B() / C(), smem)
+                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                             &n, k_sweep2<B(), C(), false, S(), OUT_STAGED>, 2 * B() / C(), smem);
     });
     return e == cudaSuccess && n > 0 ? n : 1;
 }
 
-void launch_step_tma16(const KParams& p, float* src16, float* dst16, const float* fields,
-                       const FusedShape& sh, const CUtensorMap& map, int st, int* err,
-                       cudaStream_t s) {
+void launch_sweep2_16(const KParams& p, float* dst, const float* fields, const FusedShape& sh,
+                      const CUtensorMap& load_map, const StoreMaps& store_maps, int st, int* err,
+                      cudaStream_t s) {
     const int tx = sh.bx - 4;
     dim3 grid((p.nx + tx - 1) / tx, (p.ny + sh.seg - 1) / sh.seg);
-    const size_t smem = tma16_smem_bytes(sh.bx, p.coupled);
-    (void)src16;
-    with_bx_st(sh.bx, st, [&](auto B, auto S) {
+    const size_t smem = sweep2_16_smem_bytes(sh.bx, sh.cpt, p.coupled);
+    with_shape16(sh.bx, sh.cpt, st, [&](auto B, auto C, auto S) {
         if (p.coupled)
-            k_sweep_tma16<B(), true, S()><<<grid, 2 * B(), smem, s>>>(map, p, dst16, fields, sh.seg, err);
+            k_sweep2<B(), C(), true, S(), OUT_STAGED><<<grid, 2 * B() / C(), smem, s>>>(
+                load_map, store_maps, p, dst, fields, sh.seg, err);
         else
-            k_sweep_tma16<B(), false, S()><<<grid, 2 * B(), smem, s>>>(map, p, dst16, fields, sh.seg, err);
+            k_sweep2<B(), C(), false, S(), OUT_STAGED><<<grid, 2 * B() / C(), smem, s>>>(
+                load_map, store_maps, p, dst, fields, sh.seg, err);
         return 0;
     });
 }
 
 void launch_step_advance(unsigned* ctr, unsigned n, cudaStream_t s) {
     k_step_advance<<<1, 1, 0, s>>>(ctr, n);
+}
+
+void launch_step_advance_many(unsigned* const* ctrs, int nctr, unsigned n, cudaStream_t s) {
+    if (nctr > 0) k_step_advance_many<<<(nctr + 127) / 128, 128, 0, s>>>(ctrs, nctr, n);
 }
 
 void launch_pack16(const KParams& p, const float* src32_alloc, float* dst16_alloc, int st,

@@ -82,6 +82,10 @@ SIGNATURES = {
     "lbm_set_launch_shape": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32]),
     "lbm_get_launch_shape": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int32),
                                             ctypes.POINTER(ctypes.c_int32)]),
+    "lbm_set_cells_per_thread": (ctypes.c_int, [_VP, ctypes.c_int32]),
+    "lbm_get_cells_per_thread": (ctypes.c_int32, [_VP]),
+    "lbm_set_store_mode": (ctypes.c_int, [_VP, ctypes.c_int32]),
+    "lbm_get_store_mode": (ctypes.c_int32, [_VP]),
     "lbm_save_state": (ctypes.c_int, [_VP, ctypes.c_char_p]),
     "lbm_load_state": (ctypes.c_int, [_VP, ctypes.c_char_p]),
     "lbm_debug_stall_next_step": (ctypes.c_int, [_VP]),
@@ -97,7 +101,11 @@ SIGNATURES = {
     "lbm_batch_run": (_VP, [_VP, ctypes.c_int32]),
     "lbm_batch_step": (ctypes.c_int, [_VP, ctypes.c_int64]),
     "lbm_batch_synchronize": (ctypes.c_int, [_VP]),
+    "lbm_batch_set_form": (ctypes.c_int, [_VP, ctypes.c_int32]),
+    "lbm_batch_get_form": (ctypes.c_int32, [_VP]),
     "lbm_batch_set_launch_shape": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32]),
+    "lbm_batch_set_cells_per_thread": (ctypes.c_int, [_VP, ctypes.c_int32]),
+    "lbm_batch_set_store_mode": (ctypes.c_int, [_VP, ctypes.c_int32]),
     "lbm_batch_get_launch_shape": (ctypes.c_int, [_VP] + [ctypes.POINTER(ctypes.c_int32)] * 4),
     "lbm_batch_autotune": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
                                           ctypes.POINTER(ctypes.c_int32),
@@ -254,6 +262,32 @@ def lbm_get_launch_shape(ctx):
     return a.value, b.value
 
 
+def lbm_set_cells_per_thread(ctx, cells: int):
+    _check(load().lbm_set_cells_per_thread(ctx, int(cells)), "lbm_set_cells_per_thread")
+
+
+def lbm_get_cells_per_thread(ctx) -> int:
+    n = load().lbm_get_cells_per_thread(ctx)
+    if n < 0:
+        raise LBMError(n, "lbm_get_cells_per_thread")
+    return n
+
+
+LBM_STORE_DIRECT = 0
+LBM_STORE_STAGED = 1
+
+
+def lbm_set_store_mode(ctx, mode: int):
+    _check(load().lbm_set_store_mode(ctx, int(mode)), "lbm_set_store_mode")
+
+
+def lbm_get_store_mode(ctx) -> int:
+    n = load().lbm_get_store_mode(ctx)
+    if n < 0:
+        raise LBMError(n, "lbm_get_store_mode")
+    return n
+
+
 def lbm_save_state(ctx, path: str):
     _check(load().lbm_save_state(ctx, path.encode()), "lbm_save_state")
 
@@ -313,6 +347,29 @@ def lbm_batch_step(b, nsteps: int):
 
 def lbm_batch_synchronize(b):
     _check(load().lbm_batch_synchronize(b), "lbm_batch_synchronize")
+
+
+LBM_BATCH_CHAINS = 0
+LBM_BATCH_PERSISTENT = 1
+
+
+def lbm_batch_set_form(b, form: int):
+    _check(load().lbm_batch_set_form(b, int(form)), "lbm_batch_set_form")
+
+
+def lbm_batch_get_form(b) -> int:
+    n = load().lbm_batch_get_form(b)
+    if n < 0:
+        raise LBMError(n, "lbm_batch_get_form")
+    return n
+
+
+def lbm_batch_set_store_mode(b, mode: int):
+    _check(load().lbm_batch_set_store_mode(b, int(mode)), "lbm_batch_set_store_mode")
+
+
+def lbm_batch_set_cells_per_thread(b, cells: int):
+    _check(load().lbm_batch_set_cells_per_thread(b, int(cells)), "lbm_batch_set_cells_per_thread")
 
 
 def lbm_batch_set_launch_shape(b, tile_x=0, seg_y=0):
@@ -426,6 +483,20 @@ class Sim:
     def set_launch_shape(self, tile_x=0, seg_y=0):
         lbm_set_launch_shape(self.ctx, tile_x, seg_y)
 
+    def set_cells_per_thread(self, cells):
+        lbm_set_cells_per_thread(self.ctx, cells)
+
+    @property
+    def cells_per_thread(self):
+        return lbm_get_cells_per_thread(self.ctx)
+
+    def set_store_mode(self, mode):
+        lbm_set_store_mode(self.ctx, mode)
+
+    @property
+    def store_mode(self):
+        return lbm_get_store_mode(self.ctx)
+
     def components(self, level=0.5):
         return lbm_count_components(self.ctx, level)
 
@@ -473,6 +544,19 @@ class Batch:
 
     def launch_shape(self):
         return lbm_batch_get_launch_shape(self.handle)
+
+    def set_cells_per_thread(self, cells):
+        lbm_batch_set_cells_per_thread(self.handle, cells)
+
+    def set_store_mode(self, mode):
+        lbm_batch_set_store_mode(self.handle, mode)
+
+    @property
+    def form(self):
+        return lbm_batch_get_form(self.handle)
+
+    def set_form(self, form):
+        lbm_batch_set_form(self.handle, form)
 
     def autotune(self, steps=16):
         return lbm_batch_autotune(self.handle, steps)

@@ -37,17 +37,28 @@ def init_all(sims, cases):
         s.init(c.phi, c.c, c.ux, c.uy, c.P)
 
 
-@pytest.mark.parametrize("shape", [(128, 32), (64, 16), (192, 24)])
-def test_batch_bitwise_equals_single_runs(shape):
+P_, C_ = lbm.LBM_BATCH_PERSISTENT, lbm.LBM_BATCH_CHAINS
+D_, S_ = lbm.LBM_STORE_DIRECT, lbm.LBM_STORE_STAGED
+
+
+@pytest.mark.parametrize("shape,cpt,out,form", [
+    ((128, 32), 1, D_, P_), ((64, 16), 1, S_, P_), ((192, 24), 2, D_, P_), ((192, 24), 2, S_, P_),
+    ((128, 32), 2, S_, C_), ((192, 24), 1, D_, C_)])
+def test_batch_bitwise_equals_single_runs(shape, cpt, out, form):
     cases = mixed_cases()
     b = lbm.Batch([c.phys for c in cases])
+    b.set_form(form)
     b.set_launch_shape(*shape)
+    b.set_cells_per_thread(cpt)
+    b.set_store_mode(out)
     init_all(b.runs, cases)
     singles = [lbm.Sim(c.phys, kernel=lbm.LBM_KERNEL_TMA) for c in cases]
     for s in singles:
         s.set_launch_shape(*shape)
+        s.set_cells_per_thread(cpt)
+        s.set_store_mode(out)
     init_all(singles, cases)
-    b.step(70)  # two captured graphs of 32 steps and 6 single launches
+    b.step(70)  # graphs of 32, 32, 4 and 2 steps
     b.sync()
     for s in singles:
         s.step(70)
@@ -141,6 +152,7 @@ def test_autotune_single_restores_state():
     tx, seg, ms = s.autotune(steps=8)
     assert tx in (64, 128, 192) and seg >= 4 and ms > 0
     assert lbm.lbm_get_launch_shape(s.ctx) == (tx, seg)
+    assert s.cells_per_thread in (1, 2)
     assert s.t == 7
     after = s.fields()
     for k in before:
@@ -148,6 +160,8 @@ def test_autotune_single_restores_state():
     # stepping on continues exactly as an untuned run with the chosen shape
     ref = lbm.Sim(case.phys, kernel=lbm.LBM_KERNEL_TMA)
     ref.set_launch_shape(tx, seg)
+    ref.set_cells_per_thread(s.cells_per_thread)
+    ref.set_store_mode(s.store_mode)
     ref.init(case.phi, case.c, case.ux, case.uy, case.P)
     ref.step(7 + 40)
     s.step(40)
@@ -164,6 +178,7 @@ def test_batch_autotune_restores_state():
     tx, seg, ms = b.autotune(steps=4)
     assert tx in (64, 128, 192) and seg >= 4 and ms > 0
     assert b.launch_shape()[:2] == (tx, seg)
+    assert b.form in (lbm.LBM_BATCH_CHAINS, lbm.LBM_BATCH_PERSISTENT)
     assert [r.t for r in b.runs] == [5] * len(cases)
     for r, f0 in zip(b.runs, before):
         f1 = r.fields()

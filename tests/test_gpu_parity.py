@@ -111,8 +111,17 @@ def test_small_and_ragged_grids(shape, walls):
         ux, uy = np.full_like(phi, 0.01), np.full_like(phi, 0.004)
     case = W.Case(f"small{nx}x{ny}w{walls}", phys, phi, c, ux, uy, None, 60)
     ref = oracle_fields(case, 60)
-    for kernel in KERNELS:
-        got = run_gpu(case, kernel).fields()
+    runs = [run_gpu(case, kernel) for kernel in KERNELS]
+    for cpt, out in ((2, lbm.LBM_STORE_STAGED), (1, lbm.LBM_STORE_STAGED), (2, lbm.LBM_STORE_DIRECT)):
+        s = lbm.Sim(case.phys, kernel=lbm.LBM_KERNEL_TMA)
+        s.set_cells_per_thread(cpt)
+        s.set_store_mode(out)
+        s.init(case.phi, case.c, case.ux, case.uy)
+        s.step(case.steps)
+        runs.append(s)
+    for run in runs:
+        got = run.fields()
+        kernel = (run.kernel, run.cells_per_thread, run.store_mode)
         errs = check_fields(got, ref)
         umax = np.abs(umag(ref)).max()
         # pointwise: every cell within 1e-4 of the field's largest magnitude
@@ -150,14 +159,22 @@ def test_sweeps_match_split(kernel):
         assert np.abs(a[k] - b[k]).max() < 1e-6, k
 
 
-@pytest.mark.parametrize("shape", [(64, 8), (64, 5), (128, 4), (128, 37), (192, 6), (192, 40)])
+D, S_ = lbm.LBM_STORE_DIRECT, lbm.LBM_STORE_STAGED
+
+
+@pytest.mark.parametrize("shape", [
+    (64, 8, 1, D), (64, 5, 1, S_), (128, 4, 1, D), (128, 37, 1, S_), (192, 6, 1, D),
+    (192, 40, 1, S_), (128, 4, 2, S_), (128, 37, 2, D), (192, 6, 2, S_), (192, 40, 2, D)])
 def test_tma_launch_shapes(shape):
-    """Every block width and segment height of the TMA sweep, on ragged grids
-    with walls and periodic y, reproduces the three-kernel chain."""
-    bx, seg = shape
+    """Every block width, segment height, cells-per-thread and store mode of
+    the TMA sweep, on ragged grids with walls and periodic y, reproduces the
+    three-kernel chain."""
+    bx, seg, cpt, out = shape
     for case in (W.lively_shear_drop(nx=131, ny=45, R=10.0), W.static_drop_cos_mode(nx=70, ny=66, R=20.0)):
         s = lbm.Sim(case.phys, kernel=lbm.LBM_KERNEL_TMA)
         s.set_launch_shape(bx, seg)
+        s.set_cells_per_thread(cpt)
+        s.set_store_mode(out)
         s.init(case.phi, case.c, case.ux, case.uy)
         s.step(80)
         a = s.pops()

@@ -46,6 +46,22 @@ def test_coupled_1000_steps(dtype, which):
 
 
 @pytest.mark.parametrize("dtype", DTYPES)
+def test_two_cells_per_thread(dtype):
+    """16-bit storage with two cells per thread (packed FP32 arithmetic) on a
+    ragged grid, against the oracle at the storage bound."""
+    case = W.lively_shear_drop(nx=203, ny=61, R=14.0)
+    ref = oracle.run_case(case, steps=600).fields()
+    for shape in ((128, 32), (192, 24)):
+        s = lbm.Sim(case.phys, dtype=dtype)
+        s.set_launch_shape(*shape)
+        s.set_cells_per_thread(2)
+        s.init(case.phi, case.c, case.ux, case.uy)
+        s.step(600)
+        e = errors(s.fields(), ref)
+        assert max(e.values()) <= BOUND[dtype], (shape, e)
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
 def test_fixed_velocity_static_drop_1000_steps(dtype):
     case = W.static_drop_cos_mode()
     ref = oracle.run_case(case, steps=1000).fields()
