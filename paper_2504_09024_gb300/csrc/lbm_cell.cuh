@@ -183,6 +183,27 @@ __device__ __forceinline__ void collide_scalars_cell(const KParams& p, VI phi_fx
     collide_scalar_dev(c, hjx, hjy, dt * nx, dt * ny, p.w_chi, ux, uy, dh, sh);
 }
 
+// The same two collisions of one cell with f and h as the two lanes of the
+// packed FP32 instructions (they share the velocity and the whole sequence of
+// operations); df[q] and dh[q] as above.
+__device__ __forceinline__ void collide_scalars_pair(const KParams& p, int phi_fx, float phi,
+                                                     float c, float nx, float ny, float ux,
+                                                     float uy, f2 fj_x, f2 fj_y, float df[9],
+                                                     float dh[9], float sf = 1.0f,
+                                                     float sh = 1.0f) {
+    float theta, theta_c;
+    interface_coeffs(p, phi_fx, c, theta, theta_c);
+    const f2 coef(p.M_phi * theta, p.D_s * theta_c);
+    f2 d[9];
+    collide_scalar_dev(f2(phi, c), fj_x, fj_y, coef * nx, coef * ny, f2(p.w_kappa, p.w_chi),
+                       f2(ux), f2(uy), d, f2(sf, sh));
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+        df[q] = d[q].x;
+        dh[q] = d[q].y;
+    }
+}
+
 // The three collisions of one cell at row j.  f and h enter as their first
 // moments (the zeroth moments are g.phi and g.c) and leave as deviation-form
 // outputs df, dh (q = 1..8); the flow populations gg are collided in place.

@@ -403,12 +403,12 @@ __device__ __forceinline__ V sigma_of_c(const KParams& p, V c) {
 // P^-1 applied to raw moments r = (00,10,01,20,02,11,21,12,22) (App. A),
 // times s (a power of two: the 16-bit storage scale, folded into the factors
 // 1/2 and 1/4 at no cost and without rounding; 1 for FP32 storage).
-template <class V>
-__device__ __forceinline__ void raw_to_pops(const V r[9], V out[9], float s = 1.0f) {
+template <class V, class SC = float>
+__device__ __forceinline__ void raw_to_pops(const V r[9], V out[9], SC s = 1.0f) {
     // factored: the eight pair sums and differences are shared by two outputs each
     const V a = r[3] - r[8], b = r[1] - r[7], c = r[4] - r[8], d = r[2] - r[6];
     const V e = r[8] + r[5], f = r[6] + r[7], g = r[8] - r[5], h = r[6] - r[7];
-    const float h2 = 0.5f * s, h4 = 0.25f * s;
+    const SC h2 = 0.5f * s, h4 = 0.25f * s;
     out[0] = ((r[0] - r[3]) - c) * s;
     out[1] = h2 * (a + b);
     out[2] = h2 * (c + d);
@@ -465,9 +465,9 @@ __device__ __forceinline__ void central_to_raw_sep(const V k[9], V ux, V uy, V r
 // the deviation are s (raw moments of the equilibrium shape at u minus those
 // at rest) plus the raw moments of F^-1(u) (0, k10~, k01~, 0, ...), so no
 // O(s) term is formed.
-template <class V, class W>
+template <class V, class W, class SC = float>
 __device__ __forceinline__ void collide_scalar_dev(V s, V jx, V jy, V qx, V qy, W w, V ux, V uy,
-                                                   V d[9], float out_scale = 1.0f) {
+                                                   V d[9], SC out_scale = 1.0f) {
     const V k10 = jx - ux * s, k01 = jy - uy * s;
     const V a = vfma(w, qx - k10, k10);
     const V b = vfma(w, qy - k01, k01);

@@ -244,6 +244,106 @@ pull_scalar_v(const float* Rm, const float* R0, const float* Rp, int cs, bool bo
     return m;
 }
 
+// Zeroth and first moments of f and h of one cell, f and h as the two lanes
+// of the packed FP32 instructions (FP32 storage: f in planes 0..8, h in
+// planes 9..17; the same increments as pull_scalar_v).
+template <int W>
+__device__ __forceinline__ ScalarMomentsV<f2, i2> pull_scalars_fh(const float* Rm, const float* R0,
+                                                                  const float* Rp, int cs, bool bot,
+                                                                  bool top, f2 inv) {
+    auto S_at = [&](const float* R, int c) {
+        return i2{__float_as_int(R[c]), __float_as_int(R[9 * W + c])};
+    };
+    auto d_at = [&](const float* R, int q, int c) { return f2(R[q * W + c], R[(9 + q) * W + c]); };
+    const i2 S0 = S_at(R0, cs);
+    f2 o[9];
+#pragma unroll
+    for (int q = 1; q < 9; ++q) o[q] = d_at(R0, q, cs);
+    const f2 w1 = (1.0f / 9.0f) * inv, w5 = (1.0f / 36.0f) * inv;
+    f2 t[9];
+    t[1] = vfma(w1, i2f(isub(S_at(R0, cs - 1), S0)), d_at(R0, 1, cs - 1));
+    t[3] = vfma(w1, i2f(isub(S_at(R0, cs + 1), S0)), d_at(R0, 3, cs + 1));
+    if (bot) {
+        t[2] = o[4];
+        t[5] = o[7];
+        t[6] = o[8];
+    } else {
+        t[2] = vfma(w1, i2f(isub(S_at(Rm, cs), S0)), d_at(Rm, 2, cs));
+        t[5] = vfma(w5, i2f(isub(S_at(Rm, cs - 1), S0)), d_at(Rm, 5, cs - 1));
+        t[6] = vfma(w5, i2f(isub(S_at(Rm, cs + 1), S0)), d_at(Rm, 6, cs + 1));
+    }
+    if (top) {
+        t[4] = o[2];
+        t[7] = o[5];
+        t[8] = o[6];
+    } else {
+        t[4] = vfma(w1, i2f(isub(S_at(Rp, cs), S0)), d_at(Rp, 4, cs));
+        t[7] = vfma(w5, i2f(isub(S_at(Rp, cs + 1), S0)), d_at(Rp, 7, cs + 1));
+        t[8] = vfma(w5, i2f(isub(S_at(Rp, cs - 1), S0)), d_at(Rp, 8, cs - 1));
+    }
+    ScalarMomentsV<f2, i2> m;
+    m.s0 = S0;
+    const f2 d13 = t[1] - t[3], d56 = t[5] - t[6], d78 = t[7] - t[8];
+    const f2 s56 = t[5] + t[6], s78 = t[7] + t[8];
+    m.inc = (((t[1] + t[3]) + (t[2] + t[4])) + (s56 + s78)) -
+            (((o[1] + o[3]) + (o[2] + o[4])) + ((o[5] + o[6]) + (o[7] + o[8])));
+    m.jx = (d13 + d56) - d78;
+    m.jy = ((t[2] - t[4]) + s56) - s78;
+    return m;
+}
+
+// The same for 16-bit storage, where a word already holds (f, h) of a cell.
+template <int ST, int W>
+__device__ __forceinline__ ScalarMomentsV<f2, i2> pull_scalars_fh16(const float* Rm,
+                                                                    const float* R0,
+                                                                    const float* Rp, int cs,
+                                                                    bool bot, bool top,
+                                                                    const KParams& p) {
+    auto S_at = [&](const float* R, int c) {
+        return i2{__float_as_int(R[c]), __float_as_int(R[P16_SH * W + c])};
+    };
+    auto d_at = [&](const float* R, int q, int c) {
+        return from_f2(unpack2<ST>(__float_as_uint(R[(P16_FH - 1 + q) * W + c])));
+    };
+    const i2 S0 = S_at(R0, cs);
+    f2 o[9];
+#pragma unroll
+    for (int q = 1; q < 9; ++q) o[q] = d_at(R0, q, cs);
+    // sums on the scaled deviations, unscaled once at the end (the weights
+    // carry the power-of-two scales)
+    const f2 w1((1.0f / 9.0f) * p.fx_inv[0] * p.qs[0], (1.0f / 9.0f) * p.fx_inv[1] * p.qs[1]);
+    const f2 w5((1.0f / 36.0f) * p.fx_inv[0] * p.qs[0], (1.0f / 36.0f) * p.fx_inv[1] * p.qs[1]);
+    f2 t[9];
+    t[1] = vfma(w1, i2f(isub(S_at(R0, cs - 1), S0)), d_at(R0, 1, cs - 1));
+    t[3] = vfma(w1, i2f(isub(S_at(R0, cs + 1), S0)), d_at(R0, 3, cs + 1));
+    if (bot) {
+        t[2] = o[4];
+        t[5] = o[7];
+        t[6] = o[8];
+    } else {
+        t[2] = vfma(w1, i2f(isub(S_at(Rm, cs), S0)), d_at(Rm, 2, cs));
+        t[5] = vfma(w5, i2f(isub(S_at(Rm, cs - 1), S0)), d_at(Rm, 5, cs - 1));
+        t[6] = vfma(w5, i2f(isub(S_at(Rm, cs + 1), S0)), d_at(Rm, 6, cs + 1));
+    }
+    if (top) {
+        t[4] = o[2];
+        t[7] = o[5];
+        t[8] = o[6];
+    } else {
+        t[4] = vfma(w1, i2f(isub(S_at(Rp, cs), S0)), d_at(Rp, 4, cs));
+        t[7] = vfma(w5, i2f(isub(S_at(Rp, cs + 1), S0)), d_at(Rp, 7, cs + 1));
+        t[8] = vfma(w5, i2f(isub(S_at(Rp, cs - 1), S0)), d_at(Rp, 8, cs - 1));
+    }
+    const f2 qi(p.qinv[0], p.qinv[1]);
+    ScalarMomentsV<f2, i2> m;
+    m.s0 = S0;
+    m.inc = ((((t[1] + t[3]) + (t[2] + t[4])) + ((t[5] + t[6]) + (t[7] + t[8]))) -
+             (((o[1] + o[3]) + (o[2] + o[4])) + ((o[5] + o[6]) + (o[7] + o[8])))) * qi;
+    m.jx = (((t[1] - t[3]) + (t[5] - t[6])) - (t[7] - t[8])) * qi;
+    m.jy = (((t[2] - t[4]) + (t[5] + t[6])) - (t[7] + t[8])) * qi;
+    return m;
+}
+
 // Post-streaming shifted flow populations (FP32 storage).
 template <int CPT, int W>
 __device__ __forceinline__ void pull_flow_v(const float* Rm, const float* R0, const float* Rp,
@@ -609,7 +709,27 @@ __device__ __forceinline__ bool sweep_tile2(const CUtensorMap* tmap, const Store
                     const float* Rm = staged(r - 1);
                     const float* R0 = staged(r);
                     const float* Rp = staged(r + 1);
-                    if constexpr (!FLOW) {
+                    if constexpr (!FLOW && CPT == 1) {
+                        // one cell: f and h side by side in the packed lanes
+                        ScalarMomentsV<f2, i2> m;
+                        if constexpr (ST == ST_F32)
+                            m = pull_scalars_fh<W>(Rm, R0, Rp, cs, bot, top,
+                                                   f2(p.fx_inv[0], p.fx_inv[1]));
+                        else
+                            m = pull_scalars_fh16<ST, W>(Rm, R0, Rp, cs, bot, top, p);
+                        const uint32_t b = moment_bits(seed, gi[0], jj, p.nx);
+                        const int phi_fx = fx_add_sr(m.s0.x, m.inc.x, p.fx_scale[0], b);
+                        const int c_fx = fx_add_sr(m.s0.y, m.inc.y, p.fx_scale[1], second_bits(b));
+                        const float c = (float)c_fx * p.fx_inv[1];
+                        S.s_phi[slot * RW + w0] = phi_fx;
+                        S.s_c[slot * RW + w0] = c;
+                        S.s_sig[slot * RW + w0] = sigma_of_c(p, c);
+                        ks[0][0] = lane(m.jx, 0);
+                        ks[0][1] = lane(m.jy, 0);
+                        ks[0][2] = lane(m.jx, 1);
+                        ks[0][3] = lane(m.jy, 1);
+                        kc[0] = c_fx;
+                    } else if constexpr (!FLOW) {
                         SM mf, mh;
                         if constexpr (ST == ST_F32) {
                             mf = pull_scalar_v<CPT, W>(Rm, R0, Rp, cs, bot, top, p.fx_inv[0]);
@@ -822,13 +942,21 @@ __device__ __forceinline__ bool sweep_tile2(const CUtensorMap* tmap, const Store
                         }
                     }
                     V df[9], dh[9];
-                    collide_scalars_cell(p, phi_fx, i2f(phi_fx) * p.fx_inv[0],
-                                         ldv<CPT, 0>(S.s_c + c0 * RW, w0),
-                                         ldv<CPT, 0>(S.s_nx + n0 * RW, w0),
-                                         ldv<CPT, 0>(S.s_ny + n0 * RW, w0), ux, uy, ks[3][0],
-                                         ks[3][1], ks[3][2], ks[3][3], df, dh,
-                                         ST == ST_F32 ? 1.0f : p.qs[0],
-                                         ST == ST_F32 ? 1.0f : p.qs[1]);
+                    if constexpr (CPT == 1)
+                        collide_scalars_pair(p, phi_fx, i2f(phi_fx) * p.fx_inv[0],
+                                             S.s_c[c0 * RW + w0], S.s_nx[n0 * RW + w0],
+                                             S.s_ny[n0 * RW + w0], ux, uy,
+                                             f2(ks[3][0], ks[3][2]), f2(ks[3][1], ks[3][3]), df,
+                                             dh, ST == ST_F32 ? 1.0f : p.qs[0],
+                                             ST == ST_F32 ? 1.0f : p.qs[1]);
+                    else
+                        collide_scalars_cell(p, phi_fx, i2f(phi_fx) * p.fx_inv[0],
+                                             ldv<CPT, 0>(S.s_c + c0 * RW, w0),
+                                             ldv<CPT, 0>(S.s_nx + n0 * RW, w0),
+                                             ldv<CPT, 0>(S.s_ny + n0 * RW, w0), ux, uy, ks[3][0],
+                                             ks[3][1], ks[3][2], ks[3][3], df, dh,
+                                             ST == ST_F32 ? 1.0f : p.qs[0],
+                                             ST == ST_F32 ? 1.0f : p.qs[1]);
                     float* out = S.out_s + (w0 - 2);
                     if constexpr (OUT == OUT_DIRECT) {
                         const V s_f = as_float(phi_fx), s_h = as_float(kc[3]);
