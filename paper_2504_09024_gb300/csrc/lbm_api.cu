@@ -816,15 +816,14 @@ struct lbm_batch {
     bool coupled = true;
     int form = LBM_BATCH_PERSISTENT;
     lbm::FusedShape shape{192, 32, 1};  // shape of the persistent form
-    // persistent form: tables of run parameters, tile lists, grids
+    // persistent form: tables of run parameters and tilings, grids
     int ntab = 0;
     lbm::BatchTable* htab = nullptr;    // [ntab]
-    int* tab_off = nullptr;             // [ntab + 1] tile-list offsets
     int* tab_blocks = nullptr;          // [ntab] grid sizes
-    int nitems = 0;
+    int nitems = 0;                     // tiles of a step
     lbm::RunDesc* hdesc = nullptr;      // host copy of the run table
     lbm::RunDesc* ddesc = nullptr;
-    int4* ditems = nullptr;
+    int slot0 = -1;                     // the runs' first parameter-bank slot (-1: none)
     unsigned** dctrs = nullptr;         // the runs' step counters (device array)
     lbm::KParams* hkp = nullptr;        // the runs' parameters the graphs were built with
     int* derr = nullptr;
@@ -857,7 +856,7 @@ int batch_fail(lbm_batch* b, cudaError_t e) {
     return LBM_ERR_CUDA;
 }
 
-// Tensor maps, parameter tables, tile lists and grids of the persistent form
+// Tensor maps, parameter tables, tilings and grids of the persistent form
 // for its current launch shape; run tables to the device.
 int batch_build_tiles(lbm_batch* b) {
     batch_drop_graphs(b);
@@ -869,71 +868,57 @@ int batch_build_tiles(lbm_batch* b) {
         total += (int64_t)((c->kp.nx + tx - 1) / tx) * ((c->kp.ny + b->shape.seg - 1) / b->shape.seg);
     }
     if (total > (int64_t)1 << 30) return LBM_ERR_INVALID_ARG;
-    int4* items = (int4*)std::malloc(sizeof(int4) * (size_t)total);
-    int* order = (int*)std::malloc(sizeof(int) * (size_t)b->nruns);
-    if (!items || !order) {
-        std::free(items);
-        std::free(order);
-        return LBM_ERR_NOMEM;
-    }
     const int per_sm = lbm::sweep2_batch_blocks_per_sm(bx, b->shape.cpt, b->shape.out, b->coupled);
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    int64_t n = 0;
-    for (int t = 0; t < b->ntab; ++t) {
-        const int r0 = t * lbm::BATCH_TABLE_RUNS;
-        const int r1 = std::min(b->nruns, r0 + lbm::BATCH_TABLE_RUNS);
-        // larger runs first: the tail of the persistent loop is made of small tiles
-        int m = 0;
-        for (int r = r0; r < r1; ++r) {
-            const int64_t cv = (int64_t)b->runs[r]->kp.nx * b->runs[r]->kp.ny;
-            int k = m - 1;
-            while (k >= 0 && (int64_t)b->runs[order[k]]->kp.nx * b->runs[order[k]]->kp.ny < cv) {
-                order[k + 1] = order[k];
-                --k;
-            }
-            order[k + 1] = r;
-            ++m;
-        }
-        b->tab_off[t] = (int)n;
-        for (int a = 0; a < m; ++a) {
-            const int r = order[a];
-            const lbm_ctx* c = b->runs[r];
-            const int nsx = (c->kp.nx + tx - 1) / tx, nsy = (c->kp.ny + b->shape.seg - 1) / b->shape.seg;
-            for (int sy = 0; sy < nsy; ++sy)
-                for (int sx = 0; sx < nsx; ++sx) items[n++] = make_int4(r - r0, sx, sy, r);
-        }
-        const int tiles = (int)(n - b->tab_off[t]);
-        b->tab_blocks[t] = (int)std::min<int64_t>(tiles, (int64_t)per_sm * (nsm > 0 ? nsm : 1));
-    }
-    b->tab_off[b->ntab] = (int)n;
-    std::free(order);
     for (int r = 0; r < b->nruns; ++r) {
         lbm_ctx* c = b->runs[r];
         lbm::RunDesc& d = b->hdesc[r];
         for (int k = 0; k < 2; ++k) {
             if (!lbm::make_tensor_map(&d.tmap[k], c->pop_alloc[k], c->kp, nl * 9, bx) ||
-                !lbm::make_store_maps(&d.smap[k], c->pop_alloc[k], c->kp, lbm::ST_F32, bx)) {
-                std::free(items);
+                !lbm::make_store_maps(&d.smap[k], c->pop_alloc[k], c->kp, lbm::ST_F32, bx))
                 return LBM_ERR_UNSUPPORTED;
-            }
             d.pop[k] = c->ds.pop[k];
         }
         d.fields = c->ds.fields;
         d.seg = b->shape.seg;
         d.flip = c->cur ^ b->parity;
         b->hkp[r] = c->kp;
-        b->htab[r / lbm::BATCH_TABLE_RUNS].p[r % lbm::BATCH_TABLE_RUNS] = c->kp;
     }
-    cudaFree(b->ditems);
-    b->ditems = nullptr;
-    cudaError_t e = cudaMalloc(&b->ditems, sizeof(int4) * (size_t)std::max<int64_t>(total, 1));
-    if (e == cudaSuccess)
-        e = cudaMemcpy(b->ditems, items, sizeof(int4) * (size_t)total, cudaMemcpyHostToDevice);
-    std::free(items);
-    if (e == cudaSuccess)
-        e = cudaMemcpy(b->ddesc, b->hdesc, sizeof(lbm::RunDesc) * b->nruns, cudaMemcpyHostToDevice);
+    // table t: runs t * BATCH_TABLE_RUNS + e, tiles run after run
+    for (int t = 0; t < b->ntab; ++t) {
+        lbm::BatchTable& tab = b->htab[t];
+        const int r0 = t * lbm::BATCH_TABLE_RUNS;
+        const int r1 = std::min(b->nruns, r0 + lbm::BATCH_TABLE_RUNS);
+        int first = 0;
+        for (int r = r0; r < r1; ++r) {
+            const lbm_ctx* c = b->runs[r];
+            const lbm::RunDesc& d = b->hdesc[r];
+            lbm::BatchEntry& en = tab.e[r - r0];
+            const int nsx = (c->kp.nx + tx - 1) / tx, nsy = (c->kp.ny + b->shape.seg - 1) / b->shape.seg;
+            for (int k = 0; k < 2; ++k) {
+                en.tmap[k] = &b->ddesc[r].tmap[k];
+                en.smap[k] = &b->ddesc[r].smap[k];
+                en.pop[k] = d.pop[k];
+            }
+            en.fields = d.fields;
+            en.first = first;
+            en.nsx = nsx;
+            en.seg = d.seg;
+            en.flip = d.flip;
+            first += nsx * nsy;
+        }
+        tab.nentries = r1 - r0;
+        tab.ntiles = first;
+        tab.slot0 = b->slot0 + r0;
+        b->tab_blocks[t] = std::min(first, per_sm * (nsm > 0 ? nsm : 1));
+    }
+    cudaError_t e = cudaMemcpy(b->ddesc, b->hdesc, sizeof(lbm::RunDesc) * b->nruns,
+                               cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && b->slot0 >= 0)
+        e = lbm::batch_params_upload(b->slot0, b->hkp, b->nruns, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return batch_fail(b, e);
     b->nitems = (int)total;
     b->desc_valid = true;
@@ -955,10 +940,12 @@ int batch_sync_desc(lbm_batch* b) {
     for (int r = 0; r < b->nruns; ++r) {
         b->hdesc[r].flip = b->runs[r]->cur ^ b->parity;
         b->hkp[r] = b->runs[r]->kp;
-        b->htab[r / lbm::BATCH_TABLE_RUNS].p[r % lbm::BATCH_TABLE_RUNS] = b->runs[r]->kp;
+        b->htab[r / lbm::BATCH_TABLE_RUNS].e[r % lbm::BATCH_TABLE_RUNS].flip = b->hdesc[r].flip;
     }
     cudaError_t e = cudaMemcpyAsync(b->ddesc, b->hdesc, sizeof(lbm::RunDesc) * b->nruns,
                                     cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess && b->slot0 >= 0)
+        e = lbm::batch_params_upload(b->slot0, b->hkp, b->nruns, b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     b->desc_valid = true;
     return batch_fail(b, e);
@@ -970,12 +957,8 @@ void batch_persistent_steps(lbm_batch* b, int parity, int n, cudaStream_t st) {
     for (int s = 0; s < n; ++s)
         for (int t = 0; t < b->ntab; ++t) {
             lbm::BatchTable& tab = b->htab[t];
-            const int r0 = t * lbm::BATCH_TABLE_RUNS;
-            const int r1 = std::min(b->nruns, r0 + lbm::BATCH_TABLE_RUNS);
-            for (int r = r0; r < r1; ++r) tab.p[r - r0].step_off = s;
-            lbm::launch_sweep2_batch(tab, b->ddesc, b->ditems + b->tab_off[t],
-                                     b->tab_off[t + 1] - b->tab_off[t], b->tab_blocks[t],
-                                     b->shape, b->coupled, parity ^ (s & 1), b->derr, st);
+            lbm::launch_sweep2_batch(tab, b->tab_blocks[t], b->shape, b->coupled,
+                                     parity ^ (s & 1), s, b->derr, st);
         }
     lbm::launch_step_advance_many(b->dctrs, b->nruns, (unsigned)n, st);
 }
@@ -1083,9 +1066,8 @@ int lbm_batch_create(const lbm_params* params, int32_t nruns, void* stream, lbm_
     b->hdesc = (lbm::RunDesc*)std::calloc((size_t)nruns, sizeof(lbm::RunDesc));
     b->hkp = (lbm::KParams*)std::calloc((size_t)nruns, sizeof(lbm::KParams));
     b->htab = (lbm::BatchTable*)std::calloc((size_t)b->ntab, sizeof(lbm::BatchTable));
-    b->tab_off = (int*)std::calloc((size_t)b->ntab + 1, sizeof(int));
     b->tab_blocks = (int*)std::calloc((size_t)b->ntab, sizeof(int));
-    if (!b->runs || !b->hdesc || !b->hkp || !b->htab || !b->tab_off || !b->tab_blocks) {
+    if (!b->runs || !b->hdesc || !b->hkp || !b->htab || !b->tab_blocks) {
         lbm_batch_destroy(b);
         return LBM_ERR_NOMEM;
     }
@@ -1118,6 +1100,10 @@ int lbm_batch_create(const lbm_params* params, int32_t nruns, void* stream, lbm_
         return LBM_ERR_NOMEM;
     }
     for (int r = 0; r < nruns; ++r) hctrs[r] = b->runs[r]->dstep;
+    // parameter-bank slots of the persistent form; without them the batch
+    // runs in the chains form only
+    b->slot0 = lbm::batch_params_alloc(nruns);
+    if (b->slot0 < 0) b->form = LBM_BATCH_CHAINS;
     cudaError_t e = cudaMalloc(&b->ddesc, sizeof(lbm::RunDesc) * (size_t)nruns);
     if (e == cudaSuccess) e = cudaMalloc(&b->derr, sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&b->dctrs, sizeof(unsigned*) * (size_t)nruns);
@@ -1151,15 +1137,14 @@ void lbm_batch_destroy(lbm_batch* b) {
     if (!b) return;
     if (b->stream) cudaStreamSynchronize(b->stream);
     batch_drop_graphs(b);
+    if (b->slot0 >= 0) lbm::batch_params_free(b->slot0, b->nruns);
     for (int r = 0; r < b->nruns; ++r) lbm_destroy(b->runs[r]);
     std::free(b->runs);
     std::free(b->hdesc);
     std::free(b->hkp);
     std::free(b->htab);
-    std::free(b->tab_off);
     std::free(b->tab_blocks);
     cudaFree(b->ddesc);
-    cudaFree(b->ditems);
     cudaFree(b->dctrs);
     cudaFree(b->derr);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
@@ -1199,8 +1184,13 @@ int lbm_batch_step(lbm_batch* b, int64_t nsteps) {
             for (int r = 0; r < b->nruns; ++r) {
                 b->runs[r]->kp.stall_test = 0;
                 b->hkp[r].stall_test = 0;
-                b->htab[r / lbm::BATCH_TABLE_RUNS].p[r % lbm::BATCH_TABLE_RUNS].stall_test = 0;
                 drop_graphs(b->runs[r]);
+            }
+            // (stream-ordered after the step that read the flags)
+            if (b->slot0 >= 0) {
+                const cudaError_t e2 =
+                    lbm::batch_params_upload(b->slot0, b->hkp, b->nruns, b->stream);
+                if (e2 != cudaSuccess) return batch_fail(b, e2);
             }
             stall = false;
             continue;
@@ -1246,6 +1236,7 @@ int lbm_batch_synchronize(lbm_batch* b) {
 int lbm_batch_set_form(lbm_batch* b, int32_t form) {
     if (!b || (form != LBM_BATCH_CHAINS && form != LBM_BATCH_PERSISTENT))
         return LBM_ERR_INVALID_ARG;
+    if (form == LBM_BATCH_PERSISTENT && b->slot0 < 0) return LBM_ERR_UNSUPPORTED;
     const int rc = lbm_batch_synchronize(b);
     if (rc != LBM_OK) return rc;
     b->form = form;
@@ -1441,11 +1432,13 @@ int lbm_batch_autotune(lbm_batch* b, int32_t steps, int32_t* tile_x, int32_t* se
     int* cur0 = (int*)std::calloc((size_t)b->nruns, sizeof(int));
     int64_t* step0 = (int64_t*)std::calloc((size_t)b->nruns, sizeof(int64_t));
     lbm::FusedShape* run_shape = (lbm::FusedShape*)std::calloc((size_t)b->nruns, sizeof(lbm::FusedShape));
-    if (!snap || !cur0 || !step0 || !run_shape) {
+    lbm::FusedShape* best_runs = (lbm::FusedShape*)std::calloc((size_t)b->nruns, sizeof(lbm::FusedShape));
+    if (!snap || !cur0 || !step0 || !run_shape || !best_runs) {
         std::free(snap);
         std::free(cur0);
         std::free(step0);
         std::free(run_shape);
+        std::free(best_runs);
         return LBM_ERR_NOMEM;
     }
     cudaError_t ce = cudaSuccess;
@@ -1491,13 +1484,15 @@ int lbm_batch_autotune(lbm_batch* b, int32_t steps, int32_t* tile_x, int32_t* se
     lbm::FusedShape best_shape = shape0;
     int best_form = form0;
     double best = 1e300;
-    // persistent form
+    // persistent form (when the batch holds parameter-bank slots)
     b->form = LBM_BATCH_PERSISTENT;
-    const int cand[10][3] = {{128, 1, 0}, {192, 1, 0}, {64, 1, 0}, {128, 2, 0}, {192, 2, 0},
-                             {128, 1, 1}, {192, 1, 1}, {64, 1, 1}, {128, 2, 1}, {192, 2, 1}};
-    const int segs[4] = {16, 32, 48, 64};
-    for (int a = 0; a < 10 && ce == cudaSuccess && rc == LBM_OK; ++a) {
-        for (int k = 0; k < 4 && ce == cudaSuccess && rc == LBM_OK; ++k) {
+    // block widths, cells per thread and store modes, each with a range of
+    // tile heights (the tile count against the grid decides the last wave)
+    const int ncand = b->slot0 >= 0 ? 6 : 0;
+    const int cand[6][3] = {{64, 1, 0}, {128, 1, 0}, {192, 1, 0}, {64, 1, 1}, {128, 1, 1}, {128, 2, 1}};
+    const int segs[7] = {24, 32, 40, 48, 56, 64, 80};
+    for (int a = 0; a < ncand && ce == cudaSuccess && rc == LBM_OK; ++a) {
+        for (int k = 0; k < 7 && ce == cudaSuccess && rc == LBM_OK; ++k) {
             b->shape = lbm::FusedShape{cand[a][0], segs[k], cand[a][1], cand[a][2]};
             rc = batch_build_tiles(b);
             double ms = 0.0;
@@ -1509,8 +1504,22 @@ int lbm_batch_autotune(lbm_batch* b, int32_t steps, int32_t* tile_x, int32_t* se
             }
         }
     }
-    // chains form: every grid size tuned on its first run, the shape shared
-    // by the runs of that size
+    // chains form: every grid size tuned on its first run (the shape shared
+    // by the runs of that size), then a few shapes common to all runs (with
+    // the runs' chains side by side, wider tiles can win over the shapes a
+    // run picks when it has the GPU to itself)
+    auto time_chains = [&]() {
+        for (int r = 0; r < b->nruns && rc == LBM_OK; ++r) rc = set_shape(b->runs[r], run_shape[r]);
+        b->form = LBM_BATCH_CHAINS;
+        batch_drop_graphs(b);
+        double ms = 0.0;
+        if (rc == LBM_OK) rc = time_it(ms);
+        if (rc == LBM_OK && ms < best) {
+            best = ms;
+            best_form = LBM_BATCH_CHAINS;
+            std::memcpy(best_runs, run_shape, sizeof(lbm::FusedShape) * (size_t)b->nruns);
+        }
+    };
     if (ce == cudaSuccess && rc == LBM_OK) {
         for (int r = 0; r < b->nruns && rc == LBM_OK; ++r) {
             lbm_ctx* c = b->runs[r];
@@ -1525,14 +1534,11 @@ int lbm_batch_autotune(lbm_batch* b, int32_t steps, int32_t* tile_x, int32_t* se
                 run_shape[r] = c->shape;
             }
         }
-        for (int r = 0; r < b->nruns && rc == LBM_OK; ++r) rc = set_shape(b->runs[r], run_shape[r]);
-        b->form = LBM_BATCH_CHAINS;
-        batch_drop_graphs(b);
-        double ms = 0.0;
-        if (rc == LBM_OK) rc = time_it(ms);
-        if (rc == LBM_OK && ms < best) {
-            best = ms;
-            best_form = LBM_BATCH_CHAINS;
+        if (rc == LBM_OK) time_chains();
+        const lbm::FusedShape common[3] = {{192, 38, 1, 0}, {128, 32, 1, 0}, {192, 38, 2, 0}};
+        for (int a = 0; a < 3 && ce == cudaSuccess && rc == LBM_OK; ++a) {
+            for (int r = 0; r < b->nruns; ++r) run_shape[r] = common[a];
+            time_chains();
         }
     }
     if (e0) cudaEventDestroy(e0);
@@ -1542,14 +1548,18 @@ int lbm_batch_autotune(lbm_batch* b, int32_t steps, int32_t* tile_x, int32_t* se
     std::free(cur0);
     std::free(step0);
     std::free(run_shape);
-    if (ce != cudaSuccess) return batch_fail(b, ce);
-    if (rc != LBM_OK) return rc;
+    if (ce != cudaSuccess || rc != LBM_OK) {
+        std::free(best_runs);
+        return ce != cudaSuccess ? batch_fail(b, ce) : rc;
+    }
     // keep the winner: the persistent shape always; the runs' own shapes
-    // stay tuned if the chains form won, else follow the persistent shape
+    // are the winning chains shapes if the chains form won, else follow the
+    // persistent shape
     b->form = best_form;
     b->shape = best_shape;
-    if (best_form == LBM_BATCH_PERSISTENT)
-        for (int r = 0; r < b->nruns && rc == LBM_OK; ++r) rc = set_shape(b->runs[r], best_shape);
+    for (int r = 0; r < b->nruns && rc == LBM_OK; ++r)
+        rc = set_shape(b->runs[r], best_form == LBM_BATCH_CHAINS ? best_runs[r] : best_shape);
+    std::free(best_runs);
     if (rc == LBM_OK) rc = batch_build_tiles(b);
     if (rc != LBM_OK) return rc;
     if (tile_x) *tile_x = best_shape.bx;

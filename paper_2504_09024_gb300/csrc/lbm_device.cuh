@@ -189,9 +189,10 @@ __device__ __forceinline__ uint32_t pcg_hash(uint32_t v) {
 
 // Seed of one step's roundings: the step about to be taken is the device
 // counter plus the launch's offset within its graph.
-__device__ __forceinline__ uint32_t step_seed(const KParams& p) {
-    return pcg_hash((p.step_ctr ? __ldg(p.step_ctr) : 0u) + (uint32_t)p.step_off);
+__device__ __forceinline__ uint32_t step_seed_at(const KParams& p, int step_off) {
+    return pcg_hash((p.step_ctr ? __ldg(p.step_ctr) : 0u) + (uint32_t)step_off);
 }
+__device__ __forceinline__ uint32_t step_seed(const KParams& p) { return step_seed_at(p, p.step_off); }
 
 // Random bits of cell (i, j) in one step: the step's hash offset by a Weyl
 // sequence over the cells (the golden-ratio increment).  For every cell the

@@ -41,7 +41,8 @@ struct StoreMaps {
     CUtensorMap s, f;
 };
 
-// One run of a batch, as the persistent batch kernel sees it (global memory).
+// One run of a batch: its tensor maps (in global memory, where the
+// persistent batch kernel reads them), buffers and buffer parity.
 struct alignas(128) RunDesc {
     CUtensorMap tmap[2];    // bulk-tensor load maps over the run's two population buffers
     StoreMaps smap[2];      // bulk-tensor store maps over the same buffers
@@ -51,13 +52,39 @@ struct alignas(128) RunDesc {
     int flip;               // the run reads buffer (parity ^ flip) at batch parity `parity`
 };
 
-// Parameters of up to BATCH_TABLE_RUNS runs, passed to the persistent batch
-// kernel as one kernel parameter (read through the constant cache); larger
-// batches take one launch per table per step.
+// Tiling of up to BATCH_TABLE_RUNS runs, passed to the persistent batch
+// kernel as one kernel parameter; larger batches take one launch per table
+// per step.  Entry e covers the tiles first .. first + tiles - 1 of the
+// launch, strip-major within its run (tile t: strip (t - first) % nsx,
+// segment (t - first) / nsx); the run's parameters are slot slot0 + e of the
+// batch parameter bank (constant memory, see batch_params_*).
 constexpr int BATCH_TABLE_RUNS = 64;
-struct BatchTable {
-    KParams p[BATCH_TABLE_RUNS];
+struct BatchEntry {
+    const CUtensorMap* tmap[2];   // the run's load maps (in its RunDesc, global memory)
+    const StoreMaps* smap[2];     // its store maps (same)
+    float* pop[2];                // column 0 of each of its buffers
+    const float* fields;
+    int first;      // first tile of this entry in the launch
+    int nsx;        // strips (tiles across)
+    int seg;        // rows per tile
+    int flip;       // the run reads buffer (parity ^ flip) at batch parity `parity`
 };
+struct BatchTable {
+    BatchEntry e[BATCH_TABLE_RUNS];
+    int nentries;
+    int ntiles;     // tiles of the launch
+    int slot0;      // parameter-bank slot of entry 0
+};
+static_assert(sizeof(BatchTable) <= 32764, "kernel parameters are limited to 32764 bytes");
+
+// The batch parameter bank: run parameters of the persistent batch kernel in
+// constant memory, BATCH_PARAM_SLOTS slots per device, handed out in
+// contiguous ranges (a kernel reads them with indexed constant loads, which
+// the constant cache serves as it serves kernel parameters).
+constexpr int BATCH_PARAM_SLOTS = 256;
+int batch_params_alloc(int n);               // first slot of n free ones (current device), or -1
+void batch_params_free(int first, int n);
+cudaError_t batch_params_upload(int first, const KParams* kp, int n, cudaStream_t st);
 
 // Launchers (all asynchronous on `st`).
 void launch_step_split(const KParams& p, const DevState& s, int src, cudaStream_t st);
@@ -93,11 +120,11 @@ cudaError_t configure_sweep2_16_smem();
 void launch_sweep2_16(const KParams& p, float* dst, const float* fields, const FusedShape& sh,
                       const CUtensorMap& load_map, const StoreMaps& store_maps, int st, int* err,
                       cudaStream_t s);
-// Batched step: one persistent launch over `nitems` tiles (int4: entry of
-// tab, strip, segment, run) of runs sharing the launch shape (FP32 storage).
-void launch_sweep2_batch(const BatchTable& tab, const RunDesc* runs, const int4* items,
-                         int nitems, int blocks, const FusedShape& sh, bool coupled, int parity,
-                         int* err, cudaStream_t st);
+// Batched step: one persistent launch over the tab.ntiles tiles of the runs
+// in `tab`, which share the launch shape (FP32 storage); step_off is the
+// launch's offset within its graph (the stochastic roundings' step).
+void launch_sweep2_batch(const BatchTable& tab, int blocks, const FusedShape& sh, bool coupled,
+                         int parity, int step_off, int* err, cudaStream_t st);
 int sweep2_batch_blocks_per_sm(int bx, int cpt, int out, bool coupled);
 // Advance the device step counter of the stochastic roundings by n (one
 // counter, or the counters of nctr runs).

@@ -604,12 +604,14 @@ __device__ __forceinline__ void direct_stores(float* __restrict__ dst, const KPa
 // bulk-tensor store of the row it staged; that thread waits for the store to
 // have read its staging area just before the next pass's barrier 1, so the
 // read-out overlaps the next row's moments.
+// `seed` is the hash of the step (step_seed).
 template <int BX, int CPT, bool COUPLED, int ST, int OUT>
 __device__ __forceinline__ bool sweep_tile2(const CUtensorMap* tmap, const StoreMaps* smap,
                                             const KParams& p, float* __restrict__ dst,
                                             const float* __restrict__ F, int seg, int bxi, int byi,
                                             const SweepSmem<BX, CPT, COUPLED, ST, OUT>& S,
-                                            uint32_t& issued_base, int* __restrict__ err) {
+                                            uint32_t seed, uint32_t& issued_base,
+                                            int* __restrict__ err) {
     using L = SweepLayout<BX, CPT, COUPLED, ST, OUT>;
     constexpr int SW_STAGES = L::STAGES;
     static_assert(OUT == OUT_STAGED || ST == ST_F32, "16-bit rows leave through the staging area");
@@ -646,7 +648,6 @@ __device__ __forceinline__ bool sweep_tile2(const CUtensorMap* tmap, const Store
     const int nraw = last_phys - rs + 3;
 
     const uint32_t base_k = issued_base;
-    const uint32_t seed = step_seed(p);
     auto issue = [&](int k) {  // thread 0: stage raw row rs - 1 + k
         if (k >= nraw) return;
         const int row = rs - 1 + k;
@@ -1067,7 +1068,7 @@ __global__ void __launch_bounds__(2 * BX / CPT, (sweep2_min_blocks<BX, CPT, COUP
     __syncthreads();
     uint32_t issued = 0;
     sweep_tile2<BX, CPT, COUPLED, ST, OUT>(&tmap, &smap, p, dst, F, seg, blockIdx.x, blockIdx.y,
-                                           S, issued, err);
+                                           S, step_seed(p), issued, err);
 }
 
 }  // namespace lbm

@@ -4,6 +4,7 @@
 // lbm_sweep2.cuh.
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <type_traits>
 
 #include <cudaTypedefs.h>
@@ -12,15 +13,31 @@
 
 namespace lbm {
 
+// Run parameters of the persistent batch kernel (the batch parameter bank).
+__constant__ KParams c_batch_params[BATCH_PARAM_SLOTS];
+
 // One time step of every run of a batch in one launch: each block walks the
-// flat tile list with a stride of the grid size.  Runs may differ in size and
-// parameters; run r's parameters are tab.p[r] (a kernel parameter, so they
-// are read through the constant cache), its buffers and tensor maps are in
-// runs[] (global memory).
+// tiles of the table with a stride of the grid size.  Runs may differ in size
+// and parameters; the entry of a tile is found by bisection over the table's
+// first tiles.  A run's parameters come from the parameter bank, the
+// addresses of its buffers and tensor maps from the table (a kernel
+// parameter); the maps themselves are in global memory.
+// Register budget of the persistent batch kernel.  A run's parameters come
+// from the bank by an index known only at run time, so the compiler holds
+// them in registers where the single-run kernel takes them as constant
+// operands: the one-cell form needs 130-160 registers a thread instead of 80
+// (held to 80 it spilled 200-300 bytes a thread and ran 1.6 times slower).
 template <int BX, int CPT, bool COUPLED, int OUT>
-__global__ void __launch_bounds__(2 * BX / CPT, (sweep2_min_blocks<BX, CPT, COUPLED, ST_F32, OUT>()))
-    k_sweep2_batch(const __grid_constant__ BatchTable tab, const RunDesc* __restrict__ runs,
-                   const int4* __restrict__ items, int nitems, int parity,
+constexpr int batch_min_blocks() {
+    constexpr int threads = 2 * BX / CPT;
+    constexpr int regs = CPT == 1 ? 128 : 168;
+    constexpr int by_regs = 65536 / (regs * threads);
+    return by_regs < 1 ? 1 : by_regs;
+}
+
+template <int BX, int CPT, bool COUPLED, int OUT>
+__global__ void __launch_bounds__(2 * BX / CPT, (batch_min_blocks<BX, CPT, COUPLED, OUT>()))
+    k_sweep2_batch(const __grid_constant__ BatchTable tab, int parity, int step_off,
                    int* __restrict__ err) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     // the bulk-tensor copies need the carve-up on 128-byte boundaries
@@ -36,13 +53,21 @@ __global__ void __launch_bounds__(2 * BX / CPT, (sweep2_min_blocks<BX, CPT, COUP
     }
     __syncthreads();
     uint32_t issued = 0;
-    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
-        const int4 w = items[it];  // (entry of tab, strip, segment, run)
-        const RunDesc* rd = runs + w.w;
-        const int src = parity ^ rd->flip;
+    for (int it = blockIdx.x; it < tab.ntiles; it += gridDim.x) {
+        int lo = 0, hi = tab.nentries;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (tab.e[mid].first <= it) lo = mid;
+            else hi = mid;
+        }
+        const BatchEntry& en = tab.e[lo];
+        const KParams& p = c_batch_params[tab.slot0 + lo];
+        const int local = it - en.first;
+        const int sy = local / en.nsx, sx = local - sy * en.nsx;
+        const int src = parity ^ en.flip;
         const bool ok = sweep_tile2<BX, CPT, COUPLED, ST_F32, OUT>(
-            &rd->tmap[src], &rd->smap[1 - src], tab.p[w.x], rd->pop[1 - src], rd->fields, rd->seg,
-            w.y, w.z, S, issued, err);
+            en.tmap[src], en.smap[1 - src], p, en.pop[1 - src], en.fields, en.seg, sx, sy, S,
+            step_seed_at(p, step_off), issued, err);
         if (!ok) break;
     }
 }
@@ -186,19 +211,54 @@ int sweep2_batch_blocks_per_sm(int bx, int cpt, int out, bool coupled) {
     return e == cudaSuccess && n > 0 ? n : 1;
 }
 
-void launch_sweep2_batch(const BatchTable& tab, const RunDesc* runs, const int4* items,
-                         int nitems, int blocks, const FusedShape& sh, bool coupled, int parity,
-                         int* err, cudaStream_t st) {
+void launch_sweep2_batch(const BatchTable& tab, int blocks, const FusedShape& sh, bool coupled,
+                         int parity, int step_off, int* err, cudaStream_t st) {
     const size_t smem = sweep2_f32_smem_bytes(sh.bx, sh.cpt, sh.out, coupled);
     with_shape_f32(sh.bx, sh.cpt, sh.out, [&](auto B, auto C, auto O) {
         if (coupled)
             k_sweep2_batch<B(), C(), true, O()><<<blocks, 2 * B() / C(), smem, st>>>(
-                tab, runs, items, nitems, parity, err);
+                tab, parity, step_off, err);
         else
             k_sweep2_batch<B(), C(), false, O()><<<blocks, 2 * B() / C(), smem, st>>>(
-                tab, runs, items, nitems, parity, err);
+                tab, parity, step_off, err);
         return 0;
     });
+}
+
+// Parameter-bank slots in use, per device (host bookkeeping).
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_slot_mu;
+unsigned char g_slot_used[kMaxDevices][BATCH_PARAM_SLOTS];
+}  // namespace
+
+int batch_params_alloc(int n) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return -1;
+    if (n < 1 || n > BATCH_PARAM_SLOTS) return -1;
+    std::lock_guard<std::mutex> lk(g_slot_mu);
+    for (int a = 0; a + n <= BATCH_PARAM_SLOTS; ++a) {
+        int k = 0;
+        while (k < n && !g_slot_used[dev][a + k]) ++k;
+        if (k == n) {
+            std::memset(&g_slot_used[dev][a], 1, (size_t)n);
+            return a;
+        }
+        a += k;  // skip past the used slot
+    }
+    return -1;
+}
+
+void batch_params_free(int first, int n) {
+    int dev = 0;
+    if (first < 0 || cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return;
+    std::lock_guard<std::mutex> lk(g_slot_mu);
+    std::memset(&g_slot_used[dev][first], 0, (size_t)n);
+}
+
+cudaError_t batch_params_upload(int first, const KParams* kp, int n, cudaStream_t st) {
+    return cudaMemcpyToSymbolAsync(c_batch_params, kp, sizeof(KParams) * (size_t)n,
+                                   sizeof(KParams) * (size_t)first, cudaMemcpyHostToDevice, st);
 }
 
 // Store maps over one buffer: dims {4 + nx rounded down to a multiple of 4
