@@ -19,6 +19,8 @@
 // the rest state P0 w.
 #pragma once
 
+#include <type_traits>
+
 #include <climits>
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -194,38 +196,50 @@ __device__ __forceinline__ uint32_t step_seed_at(const KParams& p, int step_off)
 }
 __device__ __forceinline__ uint32_t step_seed(const KParams& p) { return step_seed_at(p, p.step_off); }
 
-// Random bits of cell (i, j) in one step: the step's hash offset by a Weyl
-// sequence over the cells (the golden-ratio increment).  For every cell the
-// bits are uniform over steps (the step hash is), and within a step they are
-// spread evenly over the cells; one multiply-add per cell.
+// Random bits of cell (i, j) in one step: the PCG hash of the step's hash
+// offset by a Weyl sequence over the cells (the golden-ratio increment).  The
+// hash makes the bits of neighbouring cells independent: the Weyl sequence
+// alone, or a product of it with a constant, advances by a fixed fraction
+// per cell, and where that fraction is small (0.0026 per cell for one
+// constant tried) neighbouring cells round alike, their rounding errors no
+// longer cancel in the totals, and the total of c wandered about a hundred
+// times further than with independent bits (FP32 emulation and GB300 runs).
 __device__ __forceinline__ uint32_t cell_bits(uint32_t seed, int i, int j, int nx) {
-    return seed + 0x9E3779B9u * (uint32_t)(j * nx + i);
+    return pcg_hash(seed + 0x9E3779B9u * (uint32_t)(j * nx + i));
 }
 
-// 32 random bits of cell (i, j) for the roundings of its zeroth moments
-// (f: the high 16 bits, h: the low 16 bits).
+// Random bits of cell (i, j) for the rounding of phi's zeroth moment; the
+// rounding of c's takes second_bits of them.
 __device__ __forceinline__ uint32_t moment_bits(uint32_t seed, int i, int j, int nx) {
     return cell_bits(seed ^ 0x5bd1e995u, i, j, nx);
 }
 
 // Fixed-point value after adding a float increment, rounded stochastically:
-// up with probability equal to the dropped fraction, drawn from the high 16
-// bits of r16.  Rounding to nearest drops every increment below half a unit,
+// up with probability equal to the dropped fraction, drawn from the high 24
+// bits of r.  Rounding to nearest drops every increment below half a unit,
 // and in the tails of the interface profiles, where the increments are tiny
 // and of one sign step after step, that bias moves the totals of phi and c;
 // the zero-mean rounding keeps them (to the random walk of the roundings).
-__device__ __forceinline__ int fx_add_sr(int s0, float inc, float scale, uint32_t r16) {
+// The increment is split exactly into its floor and its fraction (v - floor(v)
+// is exact in FP32), and the fraction is compared with the random number:
+// adding the random number to v in FP32 instead would round the sum to the
+// float grid of v, which biases the result upwards by about a quarter of
+// that grid's spacing (0.07 units at |v| ~ 3e6 units).
+__device__ __forceinline__ int fx_add_sr(int s0, float inc, float scale, uint32_t r) {
     const float v = inc * scale;
     if (!(fabsf(v) < 1.0e9f)) return FX_INVALID;
-    const float u = (float)(r16 >> 16) * (1.0f / 65536.0f) + (1.0f / 131072.0f);
-    const unsigned r = (unsigned)s0 + (unsigned)__float2int_rd(v + u);
-    return r + (unsigned)FX_RANGE > 2u * (unsigned)FX_RANGE ? FX_INVALID : (int)r;
+    const float fl = floorf(v);
+    const float q = (v - fl) * 16777216.0f;  // the fraction in units of 2^-24
+    const unsigned up = (float)(r >> 8) < q ? 1u : 0u;
+    const unsigned sum = (unsigned)s0 + (unsigned)(int)fl + up;
+    return sum + (unsigned)FX_RANGE > 2u * (unsigned)FX_RANGE ? FX_INVALID : (int)sum;
 }
 __device__ __forceinline__ i2 fx_add_sr(i2 s0, f2 inc, float scale, uint32_t ra, uint32_t rb) {
     return i2{fx_add_sr(s0.x, inc.x, scale, ra), fx_add_sr(s0.y, inc.y, scale, rb)};
 }
-// The bits of the h lattice's rounding, from the same cell draw.
-__device__ __forceinline__ uint32_t second_bits(uint32_t b) { return b << 16; }
+// The bits of c's rounding from the same cell draw: its product with an odd
+// constant (a bijection of 32-bit words, so uniform where the draw is).
+__device__ __forceinline__ uint32_t second_bits(uint32_t b) { return b * 0x2C1B3C6Du; }
 
 // Float value of a fixed-point number (NaN for the invalid marker).
 __device__ __forceinline__ double fx_to_double(int s, float scale) {
@@ -440,22 +454,22 @@ __device__ __forceinline__ void central_to_raw(const V k[9], V ux, V uy, V r[9])
 // The same transform as central_to_raw, applied as two one-dimensional shifts
 // (F^-1(u) is the tensor product of the x and y binomial shifts): per order-2
 // triple (c0, c1, c2) -> (c0, c1 + u c0, c2 + u (c1 + (c1 + u c0))).
-template <class V>
-__device__ __forceinline__ void central_to_raw_sep(const V k[9], V ux, V uy, V r[9]) {
+__device__ __forceinline__ void central_to_raw_sep(const float k[9], float ux, float uy,
+                                                   float r[9]) {
     // x shift of the rows b = 0, 1, 2 (k indices: 00 0, 10 1, 20 3 | 01 2, 11 5, 21 6 | 02 4, 12 7, 22 8)
-    const V m10 = vfma(ux, k[0], k[1]), m20 = vfma(ux, k[1] + m10, k[3]);
-    const V m11 = vfma(ux, k[2], k[5]), m21 = vfma(ux, k[5] + m11, k[6]);
-    const V m12 = vfma(ux, k[4], k[7]), m22 = vfma(ux, k[7] + m12, k[8]);
+    const float m10 = k[1] + ux * k[0], m20 = k[3] + ux * (k[1] + m10);
+    const float m11 = k[5] + ux * k[2], m21 = k[6] + ux * (k[5] + m11);
+    const float m12 = k[7] + ux * k[4], m22 = k[8] + ux * (k[7] + m12);
     // y shift of the columns a = 0, 1, 2
     r[0] = k[0];
-    r[2] = vfma(uy, k[0], k[2]);
-    r[4] = vfma(uy, k[2] + r[2], k[4]);
+    r[2] = k[2] + uy * k[0];
+    r[4] = k[4] + uy * (k[2] + r[2]);
     r[1] = m10;
-    r[5] = vfma(uy, m10, m11);
-    r[7] = vfma(uy, m11 + r[5], m12);
+    r[5] = m11 + uy * m10;
+    r[7] = m12 + uy * (m11 + r[5]);
     r[3] = m20;
-    r[6] = vfma(uy, m20, m21);
-    r[8] = vfma(uy, m21 + r[6], m22);
+    r[6] = m21 + uy * m20;
+    r[8] = m22 + uy * (m21 + r[6]);
 }
 
 // Advection-diffusion collision returning deviation-form output:
@@ -529,53 +543,57 @@ using FlowMacro = FlowMacroT<float>;
 // collision runs on deviations: d_eta^eq = rho cs2 (M(u) - W(u)) + dP W(u).
 // out_scale: power-of-two factor applied to the output populations (16-bit
 // storage scale; 1 for FP32 storage).
-template <class V>
-__device__ __forceinline__ void collide_flow(V a[9], const FlowMacroT<V>& m, float w_zeta,
-                                             float out_scale = 1.0f) {
-    const V ux = m.ux, uy = m.uy;
-    const V ux2 = ux * ux, uy2 = uy * uy, uxy = ux * uy;
+// One cell.  The order of the operations is part of the result: in a steady
+// shear the stored populations carry the momentum with the same rounding
+// every step, and the velocity profile integrates that error.  This order
+// leaves 2.4e-6 relative velocity error after 5000 steps of the 2048 x 1024
+// drop against the FP64 oracle; a reassociated form of the same expressions
+// (products grouped differently, FMAs placed elsewhere) left 1.3e-5.
+__device__ __forceinline__ void collide_flow_cell_scalar(float a[9], const FlowMacroT<float>& m,
+                                                         float w_zeta, float out_scale) {
+    const float ux = m.ux, uy = m.uy;
+    const float ux2 = ux * ux, uy2 = uy * uy, uxy = ux * uy;
     // raw moments of the shifted populations that relax at non-unit rates
-    const V d56 = a[5] - a[6], d78 = a[7] - a[8], s56 = a[5] + a[6], s78 = a[7] + a[8];
-    const V jx = ((a[1] - a[3]) + d56) - d78;
-    const V jy = ((a[2] - a[4]) + s56) - s78;
-    const V corner = s56 + s78;
-    const V r20 = (a[1] + a[3]) + corner;
-    const V r02 = (a[2] + a[4]) + corner;
-    const V r11 = d56 + d78;
-    const V s0 = m.dPs;
+    const float jx = (a[1] - a[3]) + (a[5] - a[6]) - (a[7] - a[8]);
+    const float jy = (a[2] - a[4]) + (a[5] + a[6]) - (a[7] + a[8]);
+    const float corner = (a[5] + a[6]) + (a[7] + a[8]);
+    const float r20 = (a[1] + a[3]) + corner;
+    const float r02 = (a[2] + a[4]) + corner;
+    const float r11 = (a[5] - a[6]) + (a[7] - a[8]);
+    const float s0 = m.dPs;
     // pre-collision central moments (deviation form)
-    const V e20 = vfma(ux2, s0, r20 - 2.0f * (ux * jx));
-    const V e02 = vfma(uy2, s0, r02 - 2.0f * (uy * jy));
-    const V e11 = vfma(uxy, s0, r11 - (uy * jx + ux * jy));
+    const float e20 = r20 - 2.0f * ux * jx + ux2 * s0;
+    const float e02 = r02 - 2.0f * uy * jy + uy2 * s0;
+    const float e11 = r11 - uy * jx - ux * jy + uxy * s0;
     // equilibria (deviation form); first order -psi u (the sign reading of App. D)
-    const V R = m.rho * CS2, dP = m.dP;
-    const V RmP = R - dP;
-    const V q20 = vfma(dP, ux2 + CS2, -(R * ux2));
-    const V q02 = vfma(dP, uy2 + CS2, -(R * uy2));
-    const V q11 = -(RmP * uxy);
+    const float R = m.rho * CS2, dP = m.dP;
+    const float RmP = R - dP;
+    const float q20 = -R * ux2 + dP * (CS2 + ux2);
+    const float q02 = -R * uy2 + dP * (CS2 + uy2);
+    const float q11 = -RmP * uxy;
     // source central moments (App. D)
-    const V G = m.Fpx * ux + m.Fpy * uy;
-    const V s10 = CS2 * m.Ftx - ux * G;
-    const V s01 = CS2 * m.Fty - uy * G;
-    const V s20 = vfma(ux2 + CS2, G, (2.0f * CS2) * (m.Fpx * ux));
-    const V s02 = vfma(uy2 + CS2, G, (2.0f * CS2) * (m.Fpy * uy));
-    const V s11 = vfma(uxy, G, CS2 * (m.Fpx * uy + m.Fpy * ux));
+    const float G = m.Fpx * ux + m.Fpy * uy;
+    const float s10 = CS2 * m.Ftx - ux * G;
+    const float s01 = CS2 * m.Fty - uy * G;
+    const float s20 = 2.0f * CS2 * m.Fpx * ux + (ux2 + CS2) * G;
+    const float s02 = 2.0f * CS2 * m.Fpy * uy + (uy2 + CS2) * G;
+    const float s11 = CS2 * (m.Fpx * uy + m.Fpy * ux) + uxy * G;
     // relax in the combined basis (B): 2s at w_zeta, 2d and 11 at w_nu, rest at 1
-    const V wn = m.w_nu;
-    const V h2s = e20 + e02, h2d = e20 - e02;
-    const V t2s = vfma(w_zeta, (q20 + q02) - h2s, h2s) + (1.0f - 0.5f * w_zeta) * (s20 + s02);
-    const V t2d = vfma(wn, (q20 - q02) - h2d, h2d) + (1.0f - 0.5f * wn) * (s20 - s02);
-    V k[9];
-    k[0] = vfma(0.5f, G, dP);
-    k[1] = vfma(ux, RmP, 0.5f * s10);
-    k[2] = vfma(uy, RmP, 0.5f * s01);
+    const float wn = m.w_nu;
+    const float h2s = e20 + e02, h2d = e20 - e02;
+    const float t2s = h2s + w_zeta * ((q20 + q02) - h2s) + (1.0f - 0.5f * w_zeta) * (s20 + s02);
+    const float t2d = h2d + wn * ((q20 - q02) - h2d) + (1.0f - 0.5f * wn) * (s20 - s02);
+    float k[9];
+    k[0] = dP + 0.5f * G;
+    k[1] = ux * RmP + 0.5f * s10;
+    k[2] = uy * RmP + 0.5f * s01;
     k[3] = 0.5f * (t2s + t2d);
     k[4] = 0.5f * (t2s - t2d);
-    k[5] = vfma(wn, q11 - e11, e11) + (1.0f - 0.5f * wn) * s11;
-    k[6] = RmP * ((ux2 + CS2) * uy);
-    k[7] = RmP * ((uy2 + CS2) * ux);
-    k[8] = vfma(dP, (ux2 + CS2) * (uy2 + CS2), -(R * vfma(ux2, uy2, CS2 * (ux2 + uy2))));
-    V r[9];
+    k[5] = e11 + wn * (q11 - e11) + (1.0f - 0.5f * wn) * s11;
+    k[6] = RmP * (ux2 + CS2) * uy;
+    k[7] = RmP * (uy2 + CS2) * ux;
+    k[8] = -R * (ux2 * uy2 + CS2 * (ux2 + uy2)) + dP * (ux2 + CS2) * (uy2 + CS2);
+    float r[9];
     central_to_raw_sep(k, ux, uy, r);
     // The raw first moments of the post-collision state are exactly
     // rho cs2 u + cs2 F_t / 2 = j + cs2 F_t (j: pre-collision momentum, with
@@ -583,9 +601,42 @@ __device__ __forceinline__ void collide_flow(V a[9], const FlowMacroT<V>& m, flo
     // forward without passing through the rounded u: re-forming it from u
     // every step adds the rounding of u to the momentum, and for a slowly
     // varying flow that rounding repeats step after step and accumulates.
-    r[1] = vfma(CS2, m.Ftx, jx);
-    r[2] = vfma(CS2, m.Fty, jy);
+    // Explicit FMAs: every kernel that inlines this rounds it the same way.
+    r[1] = __fmaf_rn(CS2, m.Ftx, jx);
+    r[2] = __fmaf_rn(CS2, m.Fty, jy);
     raw_to_pops(r, a, out_scale);
+}
+
+// The same collision for one or two cells: two cells are collided lane by
+// lane with the one-cell code, so that every cell's result is the same bits
+// whatever the cells per thread.
+template <class V>
+__device__ __forceinline__ void collide_flow(V a[9], const FlowMacroT<V>& m, float w_zeta,
+                                             float out_scale = 1.0f) {
+    if constexpr (std::is_same<V, float>::value) {
+        collide_flow_cell_scalar(a, m, w_zeta, out_scale);
+    } else {
+#pragma unroll
+        for (int k = 0; k < Lanes<V>::n; ++k) {
+            float ak[9];
+#pragma unroll
+            for (int q = 0; q < 9; ++q) ak[q] = lane(a[q], k);
+            FlowMacroT<float> mk;
+            mk.ux = lane(m.ux, k);
+            mk.uy = lane(m.uy, k);
+            mk.rho = lane(m.rho, k);
+            mk.dP = lane(m.dP, k);
+            mk.dPs = lane(m.dPs, k);
+            mk.Ftx = lane(m.Ftx, k);
+            mk.Fty = lane(m.Fty, k);
+            mk.Fpx = lane(m.Fpx, k);
+            mk.Fpy = lane(m.Fpy, k);
+            mk.w_nu = lane(m.w_nu, k);
+            collide_flow_cell_scalar(ak, mk, w_zeta, out_scale);
+#pragma unroll
+            for (int q = 0; q < 9; ++q) set_lane(a[q], k, ak[q]);
+        }
+    }
 }
 
 // Moving-wall term added when a flow population is written into a slot that
