@@ -360,7 +360,9 @@ int surr_predict(surr_ctx *ctx, const float *X, int32_t n, float *D_out, float *
 int surr_grad(surr_ctx *ctx, const float *X, const float *yD, const float *yB, int32_t n,
               float *grads, double *loss);
 /* `epochs` full-batch Adam steps on the n samples with learning rate lr;
- * loss_out (nullable): loss after the last step. */
+ * loss_out (nullable): loss after the last step.  The step's launches are
+ * captured once into a CUDA graph (kept for the next call with the same n
+ * and lr) and the graph is replayed once per epoch. */
 int surr_train(surr_ctx *ctx, const float *X, const float *yD, const float *yB, int32_t n,
                int32_t epochs, float lr, double *loss_out);
 
@@ -377,25 +379,29 @@ int surr_train(surr_ctx *ctx, const float *X, const float *yD, const float *yB, 
  * phi, c, ux, uy: device float64 [ny][nx] fields (inputs, not modified).
  * walls_y: 0 periodic y (circular-mean centroid), 1 walls (plain mean).
  * beta, c_max: Langmuir parameters for the sigma < 0 count (Eq. EOS).
+ * phi_a, phi_b: the bulk phases (drop, matrix), as in lbm_params.
  * result: device array of LBM_FIELD_STATS_LEN doubles, written in full:
  *   [0] sum phi  [1] sum c  [2] xc  [3] yc  [4] non-finite cells
  *   [5] cells with sigma < 0  [6] max |u|  [7] Ixx  [8] Iyy  [9] Ixy
- *   [10] L  [11] B  [12] D   (moments, L, B, D as in lbm_diag, of the drop
- *   indicator clip(phi, 0, 1): phases phi_a = 1 and phi_b = 0)
+ *   [10] L  [11] B  [12] D   (centroid, moments, L, B, D as in lbm_diag, of
+ *   the drop indicator clip((phi - phi_b) / (phi_a - phi_b), 0, 1))
  * stream: cudaStream_t to run on (NULL: the legacy default stream).
- * Asynchronous on `stream`.  The first call on a device looks up the device
- * address of the scratch array (cudaGetSymbolAddress) with that device
- * current; make that first call before any stream capture.  Every call
+ * Asynchronous on `stream`.  The first call in a CUDA context looks up the
+ * device address of the scratch array (cudaGetSymbolAddress) and keeps it
+ * for that context (by context ID, so a reset or new context looks it up
+ * again); make that first call before any stream capture.  Every call
  * overwrites the scratch before reading it, so nothing needs clearing, but
  * calls that overlap on the GPU share the array and race.
  * Errors: INVALID_ARG (NULL pointer, nx or ny < 1, nx * ny >
- * LBM_NOALLOC_MAX_CELLS, bad walls_y or c_max), CUDA. */
+ * LBM_NOALLOC_MAX_CELLS, bad walls_y or c_max, phi_a == phi_b or not
+ * finite), CUDA. */
 #define LBM_FIELD_STATS_LEN 13
 #define LBM_NOALLOC_MAX_BLOCKS 1024
 #define LBM_NOALLOC_MAX_CELLS 1073741824
 int lbm_field_stats_noalloc(const double *phi, const double *c, const double *ux,
                             const double *uy, int32_t nx, int32_t ny, int32_t walls_y,
-                            double beta, double c_max, double *result, void *stream);
+                            double beta, double c_max, double phi_a, double phi_b,
+                            double *result, void *stream);
 
 /* Static description of an error code. */
 const char *lbm_strerror(int code);

@@ -91,7 +91,7 @@ SIGNATURES = {
     "lbm_debug_stall_next_step": (ctypes.c_int, [_VP]),
     "lbm_field_stats_noalloc": (ctypes.c_int, [_DP, _DP, _DP, _DP, ctypes.c_int32, ctypes.c_int32,
                                                ctypes.c_int32, ctypes.c_double, ctypes.c_double,
-                                               _DP, _VP]),
+                                               ctypes.c_double, ctypes.c_double, _DP, _VP]),
     "lbm_autotune": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
                                     ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double)]),
     "lbm_batch_create": (ctypes.c_int, [ctypes.POINTER(lbm_params), ctypes.c_int32, _VP,
@@ -300,12 +300,15 @@ def lbm_debug_stall_next_step(ctx):
     _check(load().lbm_debug_stall_next_step(ctx), "lbm_debug_stall_next_step")
 
 
-def lbm_field_stats_noalloc(phi, c, ux, uy, nx, ny, walls_y, beta, c_max, result, stream=None):
+def lbm_field_stats_noalloc(phi, c, ux, uy, nx, ny, walls_y, beta, c_max, result, stream=None,
+                            phi_a=1.0, phi_b=0.0):
     """FP64 field statistics of device fields into the device array `result`
-    (LBM_FIELD_STATS_LEN doubles) without any device allocation."""
+    (LBM_FIELD_STATS_LEN doubles) without any device allocation; phi_a and
+    phi_b are the bulk phases of the drop indicator."""
     _check(load().lbm_field_stats_noalloc(_addr(phi), _addr(c), _addr(ux), _addr(uy), int(nx),
                                           int(ny), int(walls_y), float(beta), float(c_max),
-                                          _addr(result), stream), "lbm_field_stats_noalloc")
+                                          float(phi_a), float(phi_b), _addr(result), stream),
+           "lbm_field_stats_noalloc")
 
 
 def lbm_autotune(ctx, steps=32):

@@ -33,11 +33,21 @@ def test_field_stats_noalloc_matches_diagnostics():
         lbm.lbm_get_fields_device(sim.ctx, *fields)
         sim.sync()
         lbm.lbm_field_stats_noalloc(*fields, p.nx, p.ny, p.walls_y, p.beta, p.c_max, result,
-                                    stream)
+                                    stream, phi_a=p.phi_a, phi_b=p.phi_b)
         torch.cuda.synchronize()
         got = result.cpu().numpy()
         for k, name in KEYS:
             assert abs(got[k] - ref[name]) <= 1e-12 * max(1.0, abs(ref[name])), (steps, name)
+        # other bulk phases: phi mapped affinely onto (phi_b, phi_a) = (-1, 2)
+        # has the same drop indicator, so the same centroid and shape
+        mapped = [fields[0] * 3.0 - 1.0] + fields[1:]
+        lbm.lbm_field_stats_noalloc(*mapped, p.nx, p.ny, p.walls_y, p.beta, p.c_max, result,
+                                    stream, phi_a=2.0, phi_b=-1.0)
+        torch.cuda.synchronize()
+        got = result.cpu().numpy()
+        for k, name in KEYS:
+            if name in ("xc", "yc", "L", "B", "D"):
+                assert abs(got[k] - ref[name]) <= 1e-9 * max(1.0, abs(ref[name])), (steps, name)
     sim.close()
 
 
@@ -49,3 +59,6 @@ def test_field_stats_noalloc_rejects_bad_sizes():
         with pytest.raises(lbm.LBMError) as e:
             lbm.lbm_field_stats_noalloc(x, x, x, x, nx, ny, 0, 0.0, 1.0, r)
         assert e.value.code == lbm.LBM_ERR_INVALID_ARG
+    with pytest.raises(lbm.LBMError) as e:  # equal bulk phases
+        lbm.lbm_field_stats_noalloc(x, x, x, x, 2, 2, 0, 0.0, 1.0, r, phi_a=0.5, phi_b=0.5)
+    assert e.value.code == lbm.LBM_ERR_INVALID_ARG
