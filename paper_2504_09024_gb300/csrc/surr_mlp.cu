@@ -16,6 +16,8 @@
 #include <cuda_bf16.h>
 #include <new>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/lbm.h"
 
 namespace surr {
@@ -196,12 +198,17 @@ __global__ void __launch_bounds__(256) k_linear_bwd_w(const float* __restrict__ 
 }
 
 // Adam with bias correction on the FP32 master parameters, then their BF16
-// copies (weights only are used in BF16; biases stay FP32).
+// copies (weights only are used in BF16; biases stay FP32).  The step number
+// is *t + 1, read on the device (k_to_bf16 advances *t after the step), so
+// that one captured step can be replayed.
 __global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
                        float* __restrict__ v, int count, float lr, float b1, float b2, float eps,
-                       float c1, float c2) {
+                       const long long* __restrict__ t) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= count) return;
+    const double step = (double)(*t + 1);
+    const float c1 = (float)(1.0 - pow((double)b1, step));
+    const float c2 = (float)(1.0 - pow((double)b2, step));
     const float gk = g[k];
     const float mk = b1 * m[k] + (1.0f - b1) * gk;
     const float vk = b2 * v[k] + (1.0f - b2) * gk * gk;
@@ -211,9 +218,13 @@ __global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float
     p[k] -= lr * mh / (sqrtf(vh) + eps);
 }
 
-__global__ void k_to_bf16(const float* __restrict__ p, __nv_bfloat16* __restrict__ q, int count) {
+// BF16 copies of the parameters; `tick` (nullable): the Adam step counter,
+// advanced by one.
+__global__ void k_to_bf16(const float* __restrict__ p, __nv_bfloat16* __restrict__ q, int count,
+                          long long* __restrict__ tick) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k < count) q[k] = __float2bfloat16_rn(p[k]);
+    if (tick && k == 0) *tick += 1;
 }
 
 }  // namespace surr
@@ -226,7 +237,13 @@ struct surr_ctx {
     float* grads = nullptr;
     float* m = nullptr;
     float* v = nullptr;
-    int64_t adam_t = 0;
+    long long* adam_t = nullptr;      // Adam steps taken (device counter)
+    // one captured training step (forward, backward, Adam, BF16 copies),
+    // valid for n samples and learning rate lr with the current buffers
+    cudaGraphExec_t step_graph = nullptr;
+    int graph_n = 0;
+    float graph_lr = 0.0f;
+    cudaStream_t cap_stream = nullptr;
     int cap = 0;                      // samples the activation buffers hold
     float* x = nullptr;               // inputs [cap][5]
     float* pre[NLAYER] = {};          // pre-activations per layer [cap][fout]
@@ -246,7 +263,13 @@ int fail(cudaError_t e) {
     return LBM_ERR_CUDA;
 }
 
+void drop_step_graph(surr_ctx* c) {
+    if (c->step_graph) cudaGraphExecDestroy(c->step_graph);
+    c->step_graph = nullptr;
+}
+
 void free_batch(surr_ctx* c) {
+    drop_step_graph(c);  // it refers to the activation buffers
     cudaFree(c->x);
     for (int l = 0; l < NLAYER; ++l) {
         cudaFree(c->pre[l]);
@@ -281,8 +304,9 @@ int ensure_batch(surr_ctx* c, int n) {
     return LBM_OK;
 }
 
-void refresh_bf16(surr_ctx* c) {
-    k_to_bf16<<<(OFF.total + 255) / 256, 256, 0, c->stream>>>(c->params, c->wq, OFF.total);
+void refresh_bf16(surr_ctx* c, bool tick = false) {
+    k_to_bf16<<<(OFF.total + 255) / 256, 256, 0, c->stream>>>(c->params, c->wq, OFF.total,
+                                                              tick ? c->adam_t : nullptr);
 }
 
 void forward(surr_ctx* c, int n) {
@@ -316,6 +340,42 @@ void backward(surr_ctx* c, int n) {
     }
 }
 
+// One Adam step on the n samples in the buffers.
+void train_step(surr_ctx* c, int n, float lr) {
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    forward(c, n);
+    backward(c, n);
+    k_adam<<<(OFF.total + 255) / 256, 256, 0, c->stream>>>(c->params, c->grads, c->m, c->v,
+                                                           OFF.total, lr, b1, b2, eps, c->adam_t);
+    refresh_bf16(c, true);
+}
+
+// The step as a graph (captured on the private stream; replayed on c->stream).
+int build_step_graph(surr_ctx* c, int n, float lr) {
+    drop_step_graph(c);
+    if (!c->cap_stream &&
+        cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+        return fail(cudaGetLastError());
+    const cudaStream_t saved = c->stream;
+    c->stream = c->cap_stream;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        train_step(c, n, lr);
+        e = cudaStreamEndCapture(c->cap_stream, &g);
+    }
+    c->stream = saved;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&c->step_graph, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        c->step_graph = nullptr;
+        return fail(e);
+    }
+    c->graph_n = n;
+    c->graph_lr = lr;
+    return LBM_OK;
+}
+
 int upload_batch(surr_ctx* c, const float* X, const float* yD, const float* yB, int n) {
     int rc = ensure_batch(c, n);
     if (rc != LBM_OK) return rc;
@@ -325,6 +385,30 @@ int upload_batch(surr_ctx* c, const float* X, const float* yD, const float* yB, 
         e = cudaMemcpyAsync(c->yD, yD, sizeof(float) * n, cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess && yB)
         e = cudaMemcpyAsync(c->yB, yB, sizeof(float) * n, cudaMemcpyHostToDevice, c->stream);
+    return fail(e);
+}
+
+// The body of surr_train (arguments checked).
+int train_epochs(surr_ctx* c, const float* X, const float* yD, const float* yB, int n, int epochs,
+                 float lr, double* loss_out) {
+    int rc = upload_batch(c, X, yD, yB, n);
+    if (rc != LBM_OK) return rc;
+    // the step's launches are captured once and the graph replayed per epoch
+    if (epochs > 0 && (!c->step_graph || c->graph_n != n || c->graph_lr != lr)) {
+        rc = build_step_graph(c, n, lr);
+        if (rc != LBM_OK) return rc;
+    }
+    cudaError_t e = cudaSuccess;
+    for (int ep = 0; ep < epochs && e == cudaSuccess; ++ep)
+        e = cudaGraphLaunch(c->step_graph, c->stream);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e == cudaSuccess && loss_out) {
+        // loss of the parameters after the last update
+        forward(c, n);
+        backward(c, n);
+        e = cudaMemcpyAsync(loss_out, c->loss, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     return fail(e);
 }
 
@@ -344,7 +428,8 @@ int surr_create(uint64_t seed, void* stream, surr_ctx** out) {
     if (cudaMalloc(&c->params, pb) != cudaSuccess || cudaMalloc(&c->grads, pb) != cudaSuccess ||
         cudaMalloc(&c->m, pb) != cudaSuccess || cudaMalloc(&c->v, pb) != cudaSuccess ||
         cudaMalloc(&c->wq, sizeof(__nv_bfloat16) * OFF.total) != cudaSuccess ||
-        cudaMalloc(&c->loss, sizeof(double)) != cudaSuccess) {
+        cudaMalloc(&c->loss, sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&c->adam_t, sizeof(long long)) != cudaSuccess) {
         cudaGetLastError();
         surr_destroy(c);
         return LBM_ERR_NOMEM;
@@ -395,6 +480,8 @@ void surr_destroy(surr_ctx* c) {
     cudaFree(c->v);
     cudaFree(c->wq);
     cudaFree(c->loss);
+    cudaFree(c->adam_t);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     delete c;
 }
 
@@ -404,7 +491,7 @@ int surr_set_params(surr_ctx* c, const float* params) {
     cudaError_t e = cudaMemcpyAsync(c->params, params, pb, cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->m, 0, pb, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->v, 0, pb, c->stream);
-    c->adam_t = 0;
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->adam_t, 0, sizeof(long long), c->stream);
     if (e != cudaSuccess) return fail(e);
     refresh_bf16(c);
     return fail(cudaStreamSynchronize(c->stream));
@@ -457,28 +544,10 @@ int surr_grad(surr_ctx* c, const float* X, const float* yD, const float* yB, int
 int surr_train(surr_ctx* c, const float* X, const float* yD, const float* yB, int32_t n,
                int32_t epochs, float lr, double* loss_out) {
     if (!c || !X || !yD || !yB || n < 1 || epochs < 0 || !(lr > 0.0f)) return LBM_ERR_INVALID_ARG;
-    int rc = upload_batch(c, X, yD, yB, n);
-    if (rc != LBM_OK) return rc;
-    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
-    for (int ep = 0; ep < epochs; ++ep) {
-        forward(c, n);
-        backward(c, n);
-        c->adam_t += 1;
-        const float c1 = (float)(1.0 - std::pow((double)b1, (double)c->adam_t));
-        const float c2 = (float)(1.0 - std::pow((double)b2, (double)c->adam_t));
-        k_adam<<<(OFF.total + 255) / 256, 256, 0, c->stream>>>(c->params, c->grads, c->m, c->v,
-                                                               OFF.total, lr, b1, b2, eps, c1, c2);
-        refresh_bf16(c);
-    }
-    cudaError_t e = cudaGetLastError();
-    if (e == cudaSuccess && loss_out) {
-        // loss of the parameters after the last update
-        forward(c, n);
-        backward(c, n);
-        e = cudaMemcpyAsync(loss_out, c->loss, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
-    }
-    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-    return fail(e);
+    nvtxRangePushA("surr_train");
+    const int rc = train_epochs(c, X, yD, yB, n, epochs, lr, loss_out);
+    nvtxRangePop();
+    return rc;
 }
 
 }  // extern "C"

@@ -25,12 +25,17 @@ def test_bisection_finds_a_known_boundary():
 
 
 def test_sweep_pipeline_small():
-    rep = sweep.main(["--grid", "96x32", "--train", "48", "--points", "8",
+    rep = sweep.main(["--grid", "96x32", "--train", "48", "--heldout", "8", "--points", "8",
                       "--baseline-points", "4", "--t-star", "0.3", "--epochs", "300"])
     assert rep["train_runs"] == 48 and rep["sweep_points"] == 8
+    assert rep["heldout_points"] == 8 and 0.0 <= rep["heldout_breakup_accuracy"] <= 1.0
     assert rep["verify_runs"] == 2 * rep["predicted"]
+    # every point ends with a Ca_crit: confirmed, or found by the LBM fallback
+    assert rep["resolved"] == rep["sweep_points"]
+    assert rep["fallback_points"] == rep["sweep_points"] - rep["confirmed"]
+    assert rep["runs_per_point_with_surrogate"] == pytest.approx(
+        (rep["verify_runs"] + rep["fallback_runs"]) / rep["sweep_points"])
     # from [0.05, 0.5] to a bracket 0.1 wide: three LBM runs per point
     assert rep["baseline_runs"] == 3 * 4
-    # the network leaves two confirmation runs per point instead of three
-    assert rep["runs_per_point_with_surrogate"] <= 2.0 < rep["baseline_runs_per_point"]
     assert rep["runs_per_hour"] > 0
+    assert rep["gpu_hours_surrogate_with_training"] >= rep["gpu_hours_surrogate_search"] > 0
