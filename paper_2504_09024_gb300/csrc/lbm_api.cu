@@ -9,8 +9,19 @@
 #include <cstring>
 #include <new>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/lbm.h"
 #include "lbm_internal.h"
+
+// NVTX range over a host call (header-only NVTX: free when no profiler is
+// attached), for timelines of steps, graph replays, diagnostics and tuning.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 namespace lbm {
 cudaError_t configure_fused_smem();
@@ -454,6 +465,7 @@ int lbm_init_fields(lbm_ctx* ctx, const double* phi, const double* c, const doub
 
 int lbm_step(lbm_ctx* ctx, int64_t nsteps) {
     if (!ctx || nsteps < 0) return LBM_ERR_INVALID_ARG;
+    NvtxRange range("lbm_step");
     while (nsteps > 0) {
         if (!ctx->kp.stall_test) {
             int chunk = 0;
@@ -463,8 +475,11 @@ int lbm_step(lbm_ctx* ctx, int64_t nsteps) {
                 int rc = build_graph(ctx, ctx->cur, chunk);
                 if (rc != LBM_OK) return rc;
             }
-            if (cudaGraphLaunch(ctx->graph[chunk][ctx->cur], ctx->stream) != cudaSuccess)
-                return cuda_fail(ctx, cudaGetLastError());
+            {
+                NvtxRange replay("graph replay");
+                if (cudaGraphLaunch(ctx->graph[chunk][ctx->cur], ctx->stream) != cudaSuccess)
+                    return cuda_fail(ctx, cudaGetLastError());
+            }
             ctx->cur ^= n & 1;
             ctx->step += n;
             nsteps -= n;
@@ -556,6 +571,7 @@ int lbm_set_populations(lbm_ctx* ctx, const double* f, const double* h, const do
 
 int lbm_diagnostics(lbm_ctx* ctx, lbm_diag* out) {
     if (!ctx || !out) return LBM_ERR_INVALID_ARG;
+    NvtxRange range("lbm_diagnostics");
     const int64_t n = cells(ctx);
     int rc = ensure_stage(ctx, sizeof(double) * 5 * (size_t)n);
     if (rc != LBM_OK) return rc;
@@ -1166,6 +1182,7 @@ lbm_ctx* lbm_batch_run(lbm_batch* b, int32_t run) {
 
 int lbm_batch_step(lbm_batch* b, int64_t nsteps) {
     if (!b || nsteps < 0) return LBM_ERR_INVALID_ARG;
+    NvtxRange range("lbm_batch_step");
     int rc = batch_sync_desc(b);
     if (rc != LBM_OK) return rc;
     bool stall = false;
@@ -1343,6 +1360,7 @@ extern "C" {
 
 int lbm_autotune(lbm_ctx* ctx, int32_t steps, int32_t* tile_x, int32_t* seg_y,
                  double* ms_per_step) {
+    NvtxRange range("lbm_autotune");
     if (!ctx || steps < 1) return LBM_ERR_INVALID_ARG;
     if (ctx->kernel == LBM_KERNEL_SPLIT) return LBM_ERR_UNSUPPORTED;
     int rc = lbm_synchronize(ctx);
@@ -1424,6 +1442,7 @@ int lbm_autotune(lbm_ctx* ctx, int32_t steps, int32_t* tile_x, int32_t* seg_y,
 
 int lbm_batch_autotune(lbm_batch* b, int32_t steps, int32_t* tile_x, int32_t* seg_y,
                        double* ms_per_step) {
+    NvtxRange range("lbm_batch_autotune");
     if (!b || steps < 1) return LBM_ERR_INVALID_ARG;
     const int tsteps = (steps + GRAPH_STEPS - 1) / GRAPH_STEPS * GRAPH_STEPS;
     int rc = lbm_batch_synchronize(b);
