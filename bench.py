@@ -225,12 +225,14 @@ def run_reference(args, rank, world):
 
 
 def run_ensemble(args, rank, world, local_rank):
-    """Batched ensemble of drop-in-shear runs (uneven grids; 32-step graphs
-    of one launch chain per run, a remainder below 32 steps as one persistent
-    launch per step over all runs).  value = cell updates of all runs per
-    second; runs_per_hour converts the step time to runs of RUN_STEPS steps."""
+    """One ensemble of drop-in-shear runs (uneven grids) sharded over the
+    ranks: every run is stepped by exactly one rank (runs dealt out by cell
+    count), each rank's runs as one batch in the form and launch shape
+    lbm_batch_autotune picks, and the per-run diagnostics gathered to rank 0
+    at the end.  value = cell updates of all runs per second of the slowest
+    rank; runs_per_hour converts the step time to runs of RUN_STEPS steps."""
     import torch
-    from paper_2504_09024_gb300 import lbm, workloads as W
+    from paper_2504_09024_gb300 import ensemble, lbm, workloads as W
 
     RUN_STEPS = 20000
     torch.cuda.set_device(local_rank)
@@ -239,9 +241,11 @@ def run_ensemble(args, rank, world, local_rank):
         import torch.distributed as dist  # noqa: F811
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     nruns = int(args.workload[len("ensemble"):] or 64)
-    # every rank runs its own draw of the ensemble (weak scaling over replicas)
-    draws = W.ensemble_draws(nruns=nruns, seed=W.CASE_SEED + rank)
-    cases = [W.ensemble_case(d, steps=RUN_STEPS) for d in draws]
+    draws = W.ensemble_draws(nruns=nruns, seed=W.CASE_SEED)
+    all_cases = [W.ensemble_case(d, steps=RUN_STEPS) for d in draws]
+    ncell_all = sum(c.phys.nx * c.phys.ny for c in all_cases)
+    owned = ensemble.shard([c.phys.nx * c.phys.ny for c in all_cases], world)[rank]
+    cases = [all_cases[r] for r in owned]
     ncell = sum(c.phys.nx * c.phys.ny for c in cases)
     stream = torch.cuda.Stream()
     b = lbm.Batch([c.phys for c in cases], stream=stream.cuda_stream)
@@ -274,7 +278,7 @@ def run_ensemble(args, rank, world, local_rank):
     clk = clocks.stop()
     ms_max = max_over_ranks(e0.elapsed_time(e1), dist)
     ms_step = ms_max / args.steps
-    value = whole_job_mlups(world, ncell, args.steps, ms_max * 1e-3)
+    value = ncell_all * args.steps / (ms_max * 1e-3) / 1e6
 
     # end to end through the public API: every run initialised from pinned
     # host fields, K batched steps, every run's fields read back + diagnostics
@@ -294,31 +298,42 @@ def run_ensemble(args, rank, world, local_rank):
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     e2e_s = max_over_ranks(e2e_s, dist)
-    h2d = sum(a.numel() * 8 for h in host_in for a in h)
-    d2h = sum(a.numel() * 8 for h in host_out for a in h) + 128 * len(cases)
+    # host bytes of the whole job (each rank copies its own runs)
+    h2d = sum(c.phys.nx * c.phys.ny * 8 * 4 for c in all_cases)
+    d2h = sum(c.phys.nx * c.phys.ny * 8 * 5 for c in all_cases) + 128 * nruns
+    gathered = ensemble.gather_rows(
+        {r: [d["sum_phi"], d["sum_c"], d["D"], d["nonfinite"]] for r, d in zip(owned, diags)},
+        dist)
 
     peak, peak_kind = peaks()
     bpc = BYTES_PER_CELL[args.dtype]
     achieved = bpc * ncell / (ms_step * 1e-3) / 1e9
-    # whole 32-step graphs launch one kernel per run and step; the remainder
-    # one persistent kernel per step
-    launches = (args.steps // 32) * 32 * nruns + args.steps % 32
+    # kernels a rank launches per step: one per run in the chains form (and
+    # one counter update per graph), one per table of 64 runs in the
+    # persistent form
+    form = b.form
+    per_step = len(cases) if form == lbm.LBM_BATCH_CHAINS else (len(cases) + 63) // 64
+    launches = args.steps * per_step + (args.steps + 31) // 32
     grids = {}
-    for c in cases:
+    for c in all_cases:
         k = f"{c.phys.nx}x{c.phys.ny}"
         grids[k] = grids.get(k, 0) + 1
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
+        "scaling": "strong", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
         "config": {"workload": f"ensemble of {nruns} drop-in-shear runs", "runs": nruns,
-                   "grids": grids, "cells_per_step": ncell,
-                   "kernel": "k_sweep_tma per run in graphs, k_sweep_tma_batch for remainders",
+                   "grids": grids, "cells_per_step": ncell_all,
+                   "kernel": ("k_sweep2 per run (chains of single-run launches in graphs)"
+                              if form == lbm.LBM_BATCH_CHAINS else
+                              "k_sweep2_batch (one persistent launch per step in graphs)"),
+                   "form": "chains" if form == lbm.LBM_BATCH_CHAINS else "persistent",
                    "launch_shape": [bx, seg], "persistent_blocks": blocks, "tiles": tiles,
                    "launch_shape_from": "lbm_batch_autotune" if tuned else "command line",
                    "l2": "populations exceed the 129 MB L2; no flush",
-                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-        "runs_per_hour": world * nruns * 3600.0 / (RUN_STEPS * ms_step * 1e-3),
+                   "parallelism": (f"one ensemble sharded over {world} ranks by cell count, "
+                                   "diagnostics gathered" if world > 1 else "single GPU")},
+        "runs_per_hour": nruns * 3600.0 / (RUN_STEPS * ms_step * 1e-3),
         "run_steps": RUN_STEPS,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_kind": f"{peak_kind} hbm_gbs",
@@ -329,10 +344,12 @@ def run_ensemble(args, rank, world, local_rank):
                         "lbm_batch_step(K) + lbm_get_fields and lbm_diagnostics of every run"},
         "gpu_launches": launches,
         "clocks": clk,
-        "check": {"nonfinite": int(sum(d["nonfinite"] for d in diags))},
+        "check": ({"runs_reported": len(gathered),
+                   "nonfinite": int(sum(v[3] for v in gathered.values()))}
+                  if gathered is not None else None),
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(cases[0], args.cpu_budget)
+        line["cpu_baseline"] = cpu_baseline(all_cases[0], args.cpu_budget)
     b.close()
     if rank == 0:
         print(json.dumps(line))
@@ -393,8 +410,8 @@ def bench_single(case, dtype, args, stream, dist=None, autotune=True):
 def kernel_name(sim, dtype):
     from paper_2504_09024_gb300 import lbm
     if dtype != "f32":
-        return "k_sweep_tma16"
-    return {lbm.LBM_KERNEL_TMA: "k_sweep_tma", lbm.LBM_KERNEL_FUSED: "k_fused_sweep",
+        return "k_sweep2_16"
+    return {lbm.LBM_KERNEL_TMA: "k_sweep2", lbm.LBM_KERNEL_FUSED: "k_fused_sweep",
             lbm.LBM_KERNEL_SPLIT: "k_collide"}[sim.kernel]
 
 
@@ -532,7 +549,7 @@ def run_ours(args, rank, world, local_rank):
             line[dt] = {"value": ncell / (ms16 * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": ms16,
                         "launch_shape": list(lbm.lbm_get_launch_shape(s16.ctx)),
                         "vs_f32": ms_step / ms16,
-                        "roofline": roofline(dt, ncell, ms16, "k_sweep_tma16")}
+                        "roofline": roofline(dt, ncell, ms16, "k_sweep2_16")}
             s16.close()
         line["ensemble64"] = ensemble_comparison(args, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

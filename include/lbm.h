@@ -204,8 +204,9 @@ int lbm_get_launch_shape(const lbm_ctx *ctx, int32_t *tile_x, int32_t *seg_y);
 
 /* Cells per thread of the TMA sweep: 1, or 2 horizontally adjacent cells
  * whose arithmetic runs on the packed two-lane FP32 instructions (tile_x 128
- * or 192).  Both forms compute the same expressions per cell; they differ
- * only in where the compiler fuses a multiply and an add (rounding).
+ * or 192).  Both forms compute the same expressions per cell; the flow
+ * collision gives the same bits in both, the scalar lattices may differ in
+ * the rounding of their packed sums.
  * Errors: INVALID_ARG (not 1 or 2), UNSUPPORTED (other kernels, or a block
  * width without the two-cell form). */
 int lbm_set_cells_per_thread(lbm_ctx *ctx, int32_t cells);
@@ -238,14 +239,15 @@ int lbm_load_state(lbm_ctx *ctx, const char *path);
 int lbm_debug_stall_next_step(lbm_ctx *ctx);
 
 /* ------------------------------------------------------------------------
- * Launch-shape autotuner.  Times every candidate (block width tile_x, rows
- * per block seg_y) over `steps` steps of the live state (after 2 warm-up
- * steps, CUDA events on the context's stream), restores the state, step count
- * and buffer parity after each candidate, and keeps the fastest shape.
- * Candidates: tile_x in {128, 192, 64} (TMA kernel with FP32 storage;
- * {128, 192} with 16-bit storage; 128 for FUSED), seg_y in
- * {8, 16, 32, 64, 128} plus the values that fill one and two waves of
- * resident blocks.  Needs one extra device buffer the size of a population
+ * Launch-shape autotuner.  Times every candidate (block width tile_x, cells
+ * per thread, store mode, rows per block seg_y) over `steps` steps of the
+ * live state (after 2 warm-up steps, CUDA events on the context's stream),
+ * restores the state, step count and buffer parity after each candidate,
+ * and keeps the fastest shape.  Candidates (TMA kernel): (tile_x, cells per
+ * thread) in {(128, 1), (192, 1), (64, 1), (128, 2), (192, 2)} with both
+ * store modes for FP32 storage, and (128 or 192, 1 or 2) staged for 16-bit
+ * storage; FUSED: tile_x 128.  seg_y in {8, 16, 32, 64, 128} plus the values
+ * that fill one and two waves of resident blocks.  Needs one extra device buffer the size of a population
  * buffer while it runs.  Outputs (nullable): chosen shape and its time per
  * step in milliseconds.  Synchronous.
  * Errors: INVALID_ARG (steps < 1), UNSUPPORTED (split kernel), NOMEM, CUDA,
@@ -258,9 +260,10 @@ int lbm_autotune(lbm_ctx *ctx, int32_t steps, int32_t *tile_x, int32_t *seg_y,
  * grid sizes and parameters).  A batch owns one context per run and steps
  * them in one of two forms:
  *   LBM_BATCH_PERSISTENT  every time step is one launch of a persistent TMA
- *       sweep over the tiles of all runs (larger runs first), one launch per
- *       64 runs; all runs share block width, cells per thread and rows per
- *       tile;
+ *       sweep over the tiles of all runs, one launch per 64 runs; all runs
+ *       share block width, cells per thread and rows per tile.  The runs'
+ *       parameters live in a bank in constant memory of 256 runs per
+ *       device; a batch that finds no room there has the chains form only;
  *   LBM_BATCH_CHAINS      every run is stepped by its own single-run
  *       launches with its own launch shape, the runs' launch chains spread
  *       over up to 16 side streams and running concurrently.
@@ -297,7 +300,8 @@ int lbm_batch_step(lbm_batch *b, int64_t nsteps);
 int lbm_batch_synchronize(lbm_batch *b);
 
 /* Form of the batched step (LBM_BATCH_PERSISTENT, the default, or
- * LBM_BATCH_CHAINS).  Synchronous.  Errors: INVALID_ARG. */
+ * LBM_BATCH_CHAINS).  Synchronous.  Errors: INVALID_ARG, UNSUPPORTED (the
+ * persistent form for a batch without parameter-bank slots). */
 int lbm_batch_set_form(lbm_batch *b, int32_t form);
 int32_t lbm_batch_get_form(const lbm_batch *b);
 
@@ -315,10 +319,12 @@ int lbm_batch_get_launch_shape(const lbm_batch *b, int32_t *tile_x, int32_t *seg
                                int32_t *blocks, int32_t *tiles);
 
 /* Autotuner of the batched step: the persistent form over (tile_x, cells
- * per thread) in {(128, 1), (192, 1), (64, 1), (128, 2), (192, 2)} x both
- * store modes x seg_y in {16, 32, 48, 64}, and the chains form with every run's shape from
- * lbm_autotune on one run of each grid size; the fastest form and shape are
- * kept.  Every candidate is timed over `steps` rounded up to whole 32-step
+ * per thread, store mode) in {(64, 1, direct), (128, 1, direct), (192, 1,
+ * direct), (64, 1, staged), (128, 1, staged), (128, 2, staged)} x seg_y in
+ * {24, 32, 40, 48, 56, 64, 80}; the chains form with every run's shape from
+ * lbm_autotune on one run of each grid size, and with the shapes (192, 38,
+ * 1, direct), (128, 32, 1, direct) and (192, 38, 2, direct) for every run;
+ * the fastest form and shapes are kept.  Every candidate is timed over `steps` rounded up to whole 32-step
  * graphs after one graph of warm-up, and the state, step counts and buffer
  * parities are restored after each (one snapshot buffer per run while it
  * runs).  Outputs (nullable): the persistent shape and the chosen form's time

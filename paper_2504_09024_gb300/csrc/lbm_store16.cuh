@@ -188,16 +188,8 @@ __device__ __forceinline__ void pull9_16(const float* __restrict__ Rm,
 template <int N>
 __device__ __forceinline__ void store_words(float* __restrict__ base, int64_t plane, int64_t idx,
                                             const int gs[2], int plane0, const uint32_t w[N]) {
-#ifdef LBM_EXP_INC
-    {
-        float* q = base + plane0 * plane + idx;
-#pragma unroll
-        for (int k = 0; k < N; ++k, q += plane) *q = __uint_as_float(w[k]);
-    }
-#else
 #pragma unroll
     for (int k = 0; k < N; ++k) base[(plane0 + k) * plane + idx] = __uint_as_float(w[k]);
-#endif
 #pragma unroll
     for (int g = 0; g < 2; ++g) {
         if (!gs[g]) continue;
