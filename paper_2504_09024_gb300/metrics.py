@@ -17,7 +17,7 @@ from __future__ import annotations
 import json
 import time
 
-from . import lbm
+from . import lbm, workloads as W
 
 # Algorithmic population bytes of one cell update: every population read
 # once and written once, 9 per lattice, 4 bytes in FP32 storage and 2 in the
@@ -72,3 +72,47 @@ class MetricsLog:
         self._t = time.perf_counter()
         self._step = step
         return rec
+
+
+WORKLOADS = {
+    "shear512": lambda steps: W.shear_drop_512x256(steps),
+    "shear2048": lambda steps: W.shear_drop_2048x1024(Ca=0.1, steps=steps),
+}
+
+
+def main(argv=None):
+    """Run a named workload and log a record every `every` steps, e.g. the
+    512 x 256 drop's deformation D(t) over 40,000 FP32 steps:
+
+        python -m paper_2504_09024_gb300.metrics --workload shear512 \\
+            --steps 40000 --every 2000 --out PROGRESS.jsonl
+    """
+    import argparse
+    ap = argparse.ArgumentParser(description="JSONL metrics of one run")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="shear512")
+    ap.add_argument("--steps", type=int, default=40000)
+    ap.add_argument("--every", type=int, default=2000)
+    ap.add_argument("--dtype", choices=["f32", "f16s", "bf16s"], default="f32")
+    ap.add_argument("--out", default="PROGRESS.jsonl")
+    args = ap.parse_args(argv)
+    dt = {"f32": lbm.LBM_F32, "f16s": lbm.LBM_F16S, "bf16s": lbm.LBM_BF16S}[args.dtype]
+    case = WORKLOADS[args.workload](args.steps)
+    sim = lbm.Sim(case.phys, dtype=dt)
+    sim.init(case.phi, case.c, case.ux, case.uy)
+    log = MetricsLog(args.out, sim, run=case.name, extra={"meta": case.meta})
+    gamma_dot = case.meta.get("gamma_dot")
+    rec = log.record(t_star=0.0)
+    print(json.dumps({k: rec[k] for k in ("step", "D", "sum_phi", "sum_c")}))
+    done = 0
+    while done < args.steps:
+        n = min(args.every, args.steps - done)
+        sim.step(n)
+        done += n
+        rec = log.record(t_star=done * gamma_dot if gamma_dot else None)
+        print(json.dumps({k: rec[k] for k in ("step", "D", "sum_phi", "sum_c", "MLUPS")}))
+    sim.close()
+    return 0
+
+
+if __name__ == "__main__":
+    main()
