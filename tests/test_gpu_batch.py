@@ -185,3 +185,38 @@ def test_batch_autotune_restores_state():
         for k in f0:
             np.testing.assert_array_equal(f0[k], f1[k])
     b.close()
+
+
+@pytest.mark.parametrize("form", [P_, C_])
+@pytest.mark.parametrize("shape,cpt,out", [((192, 32), 1, D_), ((128, 24), 1, S_),
+                                           ((128, 24), 2, D_)])
+def test_nonfinite_run_leaves_other_runs_unchanged(form, shape, cpt, out):
+    """A run whose state turns non-finite (here a NaN in its initial phi)
+    changes no bit of the other runs of its batch: runs of one batch share
+    blocks, shared memory and parameter slots, never data."""
+    good = W.lively_shear_drop(nx=131, ny=45, R=10.0)
+    other = W.ensemble_case(W.ensemble_draws(nruns=2, seed=5)[0], shrink=4)
+    bad_phi = good.phi.copy()
+    bad_phi[20:24, 60:70] = np.nan
+    cases = [good, dataclasses.replace(good, name="bad", phi=bad_phi), other, good]
+    b = lbm.Batch([c.phys for c in cases])
+    b.set_form(form)
+    b.set_launch_shape(*shape)
+    b.set_cells_per_thread(cpt)
+    b.set_store_mode(out)
+    init_all(b.runs, cases)
+    b.step(40)
+    b.sync()
+    assert b.runs[1].diagnostics()["nonfinite"] > 0
+    for k in (0, 2, 3):
+        s = lbm.Sim(cases[k].phys, kernel=lbm.LBM_KERNEL_TMA)
+        s.set_launch_shape(*shape)
+        s.set_cells_per_thread(cpt)
+        s.set_store_mode(out)
+        s.init(cases[k].phi, cases[k].c, cases[k].ux, cases[k].uy, cases[k].P)
+        s.step(40)
+        fr, fs = b.runs[k].fields(), s.fields()
+        for key in ("phi", "c", "ux", "uy", "P"):
+            np.testing.assert_array_equal(fr[key], fs[key], err_msg=f"run {k} {key}")
+        s.close()
+    b.close()
