@@ -840,6 +840,7 @@ struct lbm_batch {
     lbm::RunDesc* hdesc = nullptr;      // host copy of the run table
     lbm::RunDesc* ddesc = nullptr;
     int slot0 = -1;                     // the runs' first parameter-bank slot (-1: none)
+    int dev = 0;                        // the device the batch was created on
     unsigned** dctrs = nullptr;         // the runs' step counters (device array)
     lbm::KParams* hkp = nullptr;        // the runs' parameters the graphs were built with
     int* derr = nullptr;
@@ -1118,7 +1119,8 @@ int lbm_batch_create(const lbm_params* params, int32_t nruns, void* stream, lbm_
     for (int r = 0; r < nruns; ++r) hctrs[r] = b->runs[r]->dstep;
     // parameter-bank slots of the persistent form; without them the batch
     // runs in the chains form only
-    b->slot0 = lbm::batch_params_alloc(nruns);
+    if (cudaGetDevice(&b->dev) != cudaSuccess) cudaGetLastError();
+    b->slot0 = lbm::batch_params_alloc(b->dev, nruns);
     if (b->slot0 < 0) b->form = LBM_BATCH_CHAINS;
     cudaError_t e = cudaMalloc(&b->ddesc, sizeof(lbm::RunDesc) * (size_t)nruns);
     if (e == cudaSuccess) e = cudaMalloc(&b->derr, sizeof(int));
@@ -1153,7 +1155,7 @@ void lbm_batch_destroy(lbm_batch* b) {
     if (!b) return;
     if (b->stream) cudaStreamSynchronize(b->stream);
     batch_drop_graphs(b);
-    if (b->slot0 >= 0) lbm::batch_params_free(b->slot0, b->nruns);
+    if (b->slot0 >= 0) lbm::batch_params_free(b->dev, b->slot0, b->nruns);
     for (int r = 0; r < b->nruns; ++r) lbm_destroy(b->runs[r]);
     std::free(b->runs);
     std::free(b->hdesc);

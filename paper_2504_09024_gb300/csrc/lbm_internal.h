@@ -82,8 +82,8 @@ static_assert(sizeof(BatchTable) <= 32764, "kernel parameters are limited to 327
 // contiguous ranges (a kernel reads them with indexed constant loads, which
 // the constant cache serves as it serves kernel parameters).
 constexpr int BATCH_PARAM_SLOTS = 256;
-int batch_params_alloc(int n);               // first slot of n free ones (current device), or -1
-void batch_params_free(int first, int n);
+int batch_params_alloc(int dev, int n);      // first slot of n free ones on device dev, or -1
+void batch_params_free(int dev, int first, int n);
 cudaError_t batch_params_upload(int first, const KParams* kp, int n, cudaStream_t st);
 
 // Launchers (all asynchronous on `st`).

@@ -232,10 +232,8 @@ std::mutex g_slot_mu;
 unsigned char g_slot_used[kMaxDevices][BATCH_PARAM_SLOTS];
 }  // namespace
 
-int batch_params_alloc(int n) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return -1;
-    if (n < 1 || n > BATCH_PARAM_SLOTS) return -1;
+int batch_params_alloc(int dev, int n) {
+    if (dev < 0 || dev >= kMaxDevices || n < 1 || n > BATCH_PARAM_SLOTS) return -1;
     std::lock_guard<std::mutex> lk(g_slot_mu);
     for (int a = 0; a + n <= BATCH_PARAM_SLOTS; ++a) {
         int k = 0;
@@ -249,9 +247,8 @@ int batch_params_alloc(int n) {
     return -1;
 }
 
-void batch_params_free(int first, int n) {
-    int dev = 0;
-    if (first < 0 || cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return;
+void batch_params_free(int dev, int first, int n) {
+    if (first < 0 || dev < 0 || dev >= kMaxDevices) return;
     std::lock_guard<std::mutex> lk(g_slot_mu);
     std::memset(&g_slot_used[dev][first], 0, (size_t)n);
 }
