@@ -561,17 +561,40 @@ __global__ void k_diag1(KParams p, const double* __restrict__ phi, const double*
 
 // result layout: [0] sum_phi [1] sum_c [2] xc [3] yc [4] nonfinite [5] sigma_neg [6] umax
 //                [7] Ixx [8] Iyy [9] Ixy [10] L [11] B [12] D
-__global__ void k_diag_finish1(KParams p, double* __restrict__ partial, int nb,
-                               double* __restrict__ res) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    double s[DIAG_NSUM];
-    for (int k = 0; k < DIAG_NSUM; ++k) s[k] = 0.0;
-    double m = 0.0;
-    for (int b = 0; b < nb; ++b) {
-        for (int k = 0; k < DIAG_NSUM; ++k)
-            if (k != 9) s[k] += partial[(int64_t)b * DIAG_NSUM + k];
-        m = fmax(m, partial[(int64_t)b * DIAG_NSUM + 9]);
+// Sums over the nb partial rows (slot 9 by max instead when MAX9) by one
+// block of DIAG_FINISH threads: thread t adds rows t, t + DIAG_FINISH, ... in
+// order, then a fixed tree over the threads, so the result does not depend
+// on scheduling.  Thread 0 receives the totals in s.
+constexpr int DIAG_FINISH = 256;
+template <int NK, bool MAX9>
+__device__ __forceinline__ void finish_sums(const double* __restrict__ partial, int nb,
+                                            double s[NK]) {
+    __shared__ double red[NK][DIAG_FINISH];
+    for (int k = 0; k < NK; ++k) s[k] = 0.0;
+    for (int b = threadIdx.x; b < nb; b += DIAG_FINISH)
+        for (int k = 0; k < NK; ++k) {
+            const double v = partial[(int64_t)b * DIAG_NSUM + k];
+            s[k] = (MAX9 && k == 9) ? fmax(s[k], v) : s[k] + v;
+        }
+    for (int k = 0; k < NK; ++k) red[k][threadIdx.x] = s[k];
+    __syncthreads();
+    for (int w = DIAG_FINISH / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w)
+            for (int k = 0; k < NK; ++k)
+                red[k][threadIdx.x] = (MAX9 && k == 9)
+                                          ? fmax(red[k][threadIdx.x], red[k][threadIdx.x + w])
+                                          : red[k][threadIdx.x] + red[k][threadIdx.x + w];
+        __syncthreads();
     }
+    for (int k = 0; k < NK; ++k) s[k] = red[k][0];
+}
+
+__global__ void __launch_bounds__(DIAG_FINISH) k_diag_finish1(KParams p, double* __restrict__ partial,
+                                                              int nb, double* __restrict__ res) {
+    double s[DIAG_NSUM];
+    finish_sums<DIAG_NSUM, true>(partial, nb, s);
+    if (threadIdx.x != 0) return;
+    const double m = s[9];
     res[0] = s[0];
     res[1] = s[1];
     double xc = 0.5 * p.nx, yc = 0.5 * p.ny;
@@ -624,11 +647,11 @@ __global__ void k_diag2(KParams p, const double* __restrict__ phi, const double*
     block_sum<3>(v, partial + (int64_t)blockIdx.x * DIAG_NSUM);
 }
 
-__global__ void k_diag_finish2(const double* __restrict__ partial, int nb, double* __restrict__ res) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    double I[3] = {0.0, 0.0, 0.0};
-    for (int b = 0; b < nb; ++b)
-        for (int k = 0; k < 3; ++k) I[k] += partial[(int64_t)b * DIAG_NSUM + k];
+__global__ void __launch_bounds__(DIAG_FINISH) k_diag_finish2(const double* __restrict__ partial,
+                                                              int nb, double* __restrict__ res) {
+    double I[3];
+    finish_sums<3, false>(partial, nb, I);
+    if (threadIdx.x != 0) return;
     const double s0 = partial[DIAG_SW];  // sum of the drop indicator (pass 1)
     if (s0 != 0.0)
         for (int k = 0; k < 3; ++k) I[k] /= s0;
@@ -740,9 +763,9 @@ int diag_blocks(const KParams& p) {
 void launch_diag(const KParams& p, const double* phi, const double* c, const double* ux,
                  const double* uy, double* partial, int nb, double* result, cudaStream_t st) {
     k_diag1<<<nb, DIAG_THREADS, 0, st>>>(p, phi, c, ux, uy, partial);
-    k_diag_finish1<<<1, 32, 0, st>>>(p, partial, nb, result);
+    k_diag_finish1<<<1, DIAG_FINISH, 0, st>>>(p, partial, nb, result);
     k_diag2<<<nb, DIAG_THREADS, 0, st>>>(p, phi, c, ux, uy, result, partial);
-    k_diag_finish2<<<1, 32, 0, st>>>(partial, nb, result);
+    k_diag_finish2<<<1, DIAG_FINISH, 0, st>>>(partial, nb, result);
 }
 
 // ---------------------------------------------------------------------------
