@@ -215,8 +215,9 @@ int32_t lbm_get_cells_per_thread(const lbm_ctx *ctx);
 /* How the TMA sweep writes collided cells: LBM_STORE_DIRECT (each thread
  * stores its cells; four staged raw rows in flight) or LBM_STORE_STAGED (each
  * warp group stages its row in shared memory and one bulk-tensor store writes
- * it; fewer raw rows in flight).  Same results either way.  FP32 storage
- * takes both (default DIRECT), 16-bit storage STAGED only.
+ * it; fewer raw rows in flight).  Same results either way.  Defaults: DIRECT
+ * for FP32 storage, STAGED for 16-bit storage (the faster of each on the
+ * 2048 x 1024 drop); the autotuner tries both.
  * Errors: INVALID_ARG, UNSUPPORTED. */
 #define LBM_STORE_DIRECT 0
 #define LBM_STORE_STAGED 1

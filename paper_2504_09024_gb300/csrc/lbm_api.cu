@@ -708,7 +708,6 @@ int32_t lbm_get_cells_per_thread(const lbm_ctx* ctx) {
 int lbm_set_store_mode(lbm_ctx* ctx, int32_t mode) {
     if (!ctx || (mode != LBM_STORE_DIRECT && mode != LBM_STORE_STAGED)) return LBM_ERR_INVALID_ARG;
     if (ctx->kernel != LBM_KERNEL_TMA) return mode == LBM_STORE_DIRECT ? LBM_OK : LBM_ERR_UNSUPPORTED;
-    if (mode == LBM_STORE_DIRECT && ctx->st != lbm::ST_F32) return LBM_ERR_UNSUPPORTED;
     ctx->shape.out = mode;
     drop_graphs(ctx);
     return LBM_OK;
@@ -1390,8 +1389,7 @@ int lbm_autotune(lbm_ctx* ctx, int32_t steps, int32_t* tile_x, int32_t* seg_y,
         ncand = 0;
         for (int out = 0; out < 2; ++out)
             for (const auto& c : all)
-                if (lbm::sweep2_shape_ok(c[0], c[1], ctx->st) &&
-                    (out == lbm::OUT_STAGED || ctx->st == lbm::ST_F32)) {
+                if (lbm::sweep2_shape_ok(c[0], c[1], ctx->st)) {
                     cand[ncand][0] = c[0];
                     cand[ncand][1] = c[1];
                     cand[ncand][2] = out;

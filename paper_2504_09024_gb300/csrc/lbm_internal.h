@@ -114,8 +114,8 @@ void launch_sweep2_f32(const KParams& p, float* dst, const float* fields, const 
                        const CUtensorMap& load_map, const StoreMaps& store_maps, int* err,
                        cudaStream_t s);
 bool sweep2_16_shape_ok(int bx, int cpt);
-size_t sweep2_16_smem_bytes(int bx, int cpt, bool coupled);
-int sweep2_16_blocks_per_sm(int bx, int cpt, bool coupled, int st);
+size_t sweep2_16_smem_bytes(int bx, int cpt, int out, bool coupled);
+int sweep2_16_blocks_per_sm(int bx, int cpt, int out, bool coupled, int st);
 cudaError_t configure_sweep2_16_smem();
 void launch_sweep2_16(const KParams& p, float* dst, const float* fields, const FusedShape& sh,
                       const CUtensorMap& load_map, const StoreMaps& store_maps, int st, int* err,

@@ -33,11 +33,12 @@ namespace lbm {
 // Collided rows leave either by direct stores from registers (OUT_DIRECT) or
 // through a shared-memory staging area and one bulk-tensor store per row and
 // warp group (OUT_STAGED).  The staging area costs shared memory that the
-// ring of staged raw rows would otherwise use, so the ring is shorter there.
+// ring of staged raw rows would otherwise use, so the ring is shorter there;
+// the 16-bit rows are smaller, so their rings are longer.
 // Staged raw rows in the ring: the three a row's pull reads, plus rows in
 // flight ahead of them.
 __host__ __device__ constexpr int sw_stages(int st, int out) {
-    return out == OUT_DIRECT ? 4 : (st == 0 ? 3 : 5);
+    return out == OUT_DIRECT ? (st == 0 ? 4 : 6) : (st == 0 ? 3 : 5);
 }
 constexpr int SW_RING = 5;    // rows of phi, c, sigma, P* kept (and mirror copies)
 constexpr int SW_NRING = 3;   // rows of n, |grad phi|
@@ -551,6 +552,12 @@ __device__ __forceinline__ void edge_stores(const KParams& p, float* __restrict_
 // Two cells go out as one 8-byte store.
 __device__ __forceinline__ float as_float(int v) { return __int_as_float(v); }
 __device__ __forceinline__ f2 as_float(i2 v) { return f2(__int_as_float(v.x), __int_as_float(v.y)); }
+// The words of CPT cells (16-bit storage) as the value type of the stores.
+template <int CPT>
+__device__ __forceinline__ typename CellType<CPT>::V words_v(const uint32_t* w) {
+    if constexpr (CPT == 1) return __uint_as_float(w[0]);
+    else return f2(__uint_as_float(w[0]), __uint_as_float(w[1]));
+}
 
 template <int CPT, int NP, class G>
 __device__ __forceinline__ void direct_stores(float* __restrict__ dst, const KParams& p,
@@ -614,7 +621,6 @@ __device__ __forceinline__ bool sweep_tile2(const CUtensorMap* tmap, const Store
                                             int* __restrict__ err) {
     using L = SweepLayout<BX, CPT, COUPLED, ST, OUT>;
     constexpr int SW_STAGES = L::STAGES;
-    static_assert(OUT == OUT_STAGED || ST == ST_F32, "16-bit rows leave through the staging area");
     using V = typename CellType<CPT>::V;
     using VI = typename CellType<CPT>::VI;
     using SM = ScalarMomentsV<V, VI>;
@@ -884,7 +890,7 @@ __device__ __forceinline__ bool sweep_tile2(const CUtensorMap* tmap, const Store
                     // stage the row (tile column w0 - 2) and write the ghost copies,
                     // or store the cells directly
                     float* out = S.out_f + (w0 - 2);
-                    if constexpr (OUT == OUT_DIRECT) {
+                    if constexpr (OUT == OUT_DIRECT && ST == ST_F32) {
                         direct_stores<CPT, 9>(dst, p, L::NS, jc, gi, E,
                                               [&](int m) { return gg[m]; });
                     } else if constexpr (ST == ST_F32) {
@@ -901,8 +907,13 @@ __device__ __forceinline__ bool sweep_tile2(const CUtensorMap* tmap, const Store
                                                         2 * m + 1 < 9 ? lane(gg[2 * m + 1], k) : 0.0f,
                                                         word_bits(h, 9 + m));
                         }
+                        if constexpr (OUT == OUT_DIRECT) {
+                            direct_stores<CPT, 5>(dst, p, L::NS, jc, gi, E,
+                                                  [&](int m) { return words_v<CPT>(wv[m]); });
+                        } else {
 #pragma unroll
-                        for (int m = 0; m < 5; ++m) stw<CPT>(out + m * TX, 0, wv[m]);
+                            for (int m = 0; m < 5; ++m) stw<CPT>(out + m * TX, 0, wv[m]);
+                        }
                     }
                     if constexpr (OUT == OUT_STAGED) {
                         fence_proxy_async();
@@ -959,7 +970,7 @@ __device__ __forceinline__ bool sweep_tile2(const CUtensorMap* tmap, const Store
                                              ST == ST_F32 ? 1.0f : p.qs[0],
                                              ST == ST_F32 ? 1.0f : p.qs[1]);
                     float* out = S.out_s + (w0 - 2);
-                    if constexpr (OUT == OUT_DIRECT) {
+                    if constexpr (OUT == OUT_DIRECT && ST == ST_F32) {
                         const V s_f = as_float(phi_fx), s_h = as_float(kc[3]);
                         direct_stores<CPT, 18>(dst, p, 0, jc, gi, E, [&](int m) {
                             return m == 0 ? s_f : m == 9 ? s_h : m < 9 ? df[m] : dh[m - 9];
@@ -973,8 +984,6 @@ __device__ __forceinline__ bool sweep_tile2(const CUtensorMap* tmap, const Store
                             stv<CPT>(out + (9 + q) * TX, 0, dh[q]);
                         }
                     } else {
-                        sti<CPT>(reinterpret_cast<int*>(out), 0, phi_fx);
-                        sti<CPT>(reinterpret_cast<int*>(out + P16_SH * TX), 0, kc[3]);
                         uint32_t wv[8][CPT];
 #pragma unroll
                         for (int k = 0; k < CPT; ++k) {
@@ -984,8 +993,19 @@ __device__ __forceinline__ bool sweep_tile2(const CUtensorMap* tmap, const Store
                                 wv[q - 1][k] = pack2_sr<ST>(lane(df[q], k), lane(dh[q], k),
                                                             word_bits(h, q));
                         }
+                        if constexpr (OUT == OUT_DIRECT) {
+                            const V s_f = as_float(phi_fx), s_h = as_float(kc[3]);
+                            direct_stores<CPT, 10>(dst, p, 0, jc, gi, E, [&](int m) {
+                                return m == 0 ? s_f : m == P16_SH ? s_h
+                                                    : words_v<CPT>(wv[m >= P16_FH ? m - P16_FH : 0]);
+                            });
+                        } else {
+                            sti<CPT>(reinterpret_cast<int*>(out), 0, phi_fx);
+                            sti<CPT>(reinterpret_cast<int*>(out + P16_SH * TX), 0, kc[3]);
 #pragma unroll
-                        for (int q = 1; q < 9; ++q) stw<CPT>(out + (P16_FH - 1 + q) * TX, 0, wv[q - 1]);
+                            for (int q = 1; q < 9; ++q)
+                                stw<CPT>(out + (P16_FH - 1 + q) * TX, 0, wv[q - 1]);
+                        }
                     }
                     if constexpr (OUT == OUT_STAGED) {
                         fence_proxy_async();

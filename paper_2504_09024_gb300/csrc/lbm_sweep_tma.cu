@@ -292,12 +292,12 @@ bool sweep2_shape_ok(int bx, int cpt, int st) {
 
 size_t sweep2_smem_bytes(int bx, int cpt, int out, bool coupled, int st) {
     return st == ST_F32 ? sweep2_f32_smem_bytes(bx, cpt, out, coupled)
-                        : sweep2_16_smem_bytes(bx, cpt, coupled);
+                        : sweep2_16_smem_bytes(bx, cpt, out, coupled);
 }
 
 int sweep2_blocks_per_sm(int bx, int cpt, int out, bool coupled, int st) {
     return st == ST_F32 ? sweep2_f32_blocks_per_sm(bx, cpt, out, coupled)
-                        : sweep2_16_blocks_per_sm(bx, cpt, coupled, st);
+                        : sweep2_16_blocks_per_sm(bx, cpt, out, coupled, st);
 }
 
 cudaError_t configure_sweep2_smem() {

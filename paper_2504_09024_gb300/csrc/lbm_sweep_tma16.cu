@@ -81,11 +81,15 @@ __global__ void k_step_advance_many(unsigned* const* ctrs, int nctr, unsigned n)
 namespace {
 
 template <typename F>
-auto with_shape16(int bx, int cpt, int st, F&& f) {
+auto with_shape16(int bx, int cpt, int st, int out, F&& f) {
     using std::integral_constant;
+    auto go2 = [&](auto B, auto C, auto S) {
+        return out == OUT_DIRECT ? f(B, C, S, integral_constant<int, OUT_DIRECT>{})
+                                 : f(B, C, S, integral_constant<int, OUT_STAGED>{});
+    };
     auto go = [&](auto B, auto C) {
-        return st == ST_F16 ? f(B, C, integral_constant<int, ST_F16>{})
-                            : f(B, C, integral_constant<int, ST_BF16>{});
+        return st == ST_F16 ? go2(B, C, integral_constant<int, ST_F16>{})
+                            : go2(B, C, integral_constant<int, ST_BF16>{});
     };
     if (cpt == 2)
         return bx == 192 ? go(integral_constant<int, 192>{}, integral_constant<int, 2>{})
@@ -98,12 +102,12 @@ auto with_shape16(int bx, int cpt, int st, F&& f) {
 
 bool sweep2_16_shape_ok(int bx, int cpt) { return (bx == 128 || bx == 192) && (cpt == 1 || cpt == 2); }
 
-size_t sweep2_16_smem_bytes(int bx, int cpt, bool coupled) {
+size_t sweep2_16_smem_bytes(int bx, int cpt, int out, bool coupled) {
     if (!sweep2_16_shape_ok(bx, cpt)) return 0;
     // FP16 and BF16 words have the same layout
-    return with_shape16(bx, cpt, ST_F16, [&](auto B, auto C, auto) -> size_t {
-        return coupled ? SweepLayout<B(), C(), true, ST_F16, OUT_STAGED>::bytes
-                       : SweepLayout<B(), C(), false, ST_F16, OUT_STAGED>::bytes;
+    return with_shape16(bx, cpt, ST_F16, out, [&](auto B, auto C, auto, auto O) -> size_t {
+        return coupled ? SweepLayout<B(), C(), true, ST_F16, O()>::bytes
+                       : SweepLayout<B(), C(), false, ST_F16, O()>::bytes;
     });
 }
 
@@ -111,26 +115,27 @@ cudaError_t configure_sweep2_16_smem() {
     for (int bx : {128, 192})
         for (int cpt : {1, 2})
             for (int st : {ST_F16, ST_BF16})
-                with_shape16(bx, cpt, st, [&](auto B, auto C, auto S) {
-                    cudaFuncSetAttribute(k_sweep2<B(), C(), true, S(), OUT_STAGED>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)SweepLayout<B(), C(), true, S(), OUT_STAGED>::bytes);
-                    cudaFuncSetAttribute(k_sweep2<B(), C(), false, S(), OUT_STAGED>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)SweepLayout<B(), C(), false, S(), OUT_STAGED>::bytes);
-                    return 0;
-                });
+                for (int out : {OUT_DIRECT, OUT_STAGED})
+                    with_shape16(bx, cpt, st, out, [&](auto B, auto C, auto S, auto O) {
+                        cudaFuncSetAttribute(k_sweep2<B(), C(), true, S(), O()>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)SweepLayout<B(), C(), true, S(), O()>::bytes);
+                        cudaFuncSetAttribute(k_sweep2<B(), C(), false, S(), O()>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)SweepLayout<B(), C(), false, S(), O()>::bytes);
+                        return 0;
+                    });
     return cudaGetLastError();
 }
 
-int sweep2_16_blocks_per_sm(int bx, int cpt, bool coupled, int st) {
+int sweep2_16_blocks_per_sm(int bx, int cpt, int out, bool coupled, int st) {
     int n = 0;
-    const size_t smem = sweep2_16_smem_bytes(bx, cpt, coupled);
-    const cudaError_t e = with_shape16(bx, cpt, st, [&](auto B, auto C, auto S) {
+    const size_t smem = sweep2_16_smem_bytes(bx, cpt, out, coupled);
+    const cudaError_t e = with_shape16(bx, cpt, st, out, [&](auto B, auto C, auto S, auto O) {
         return coupled ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                             &n, k_sweep2<B(), C(), true, S(), OUT_STAGED>, 2 * B() / C(), smem)
+                             &n, k_sweep2<B(), C(), true, S(), O()>, 2 * B() / C(), smem)
                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                             &n, k_sweep2<B(), C(), false, S(), OUT_STAGED>, 2 * B() / C(), smem);
+                             &n, k_sweep2<B(), C(), false, S(), O()>, 2 * B() / C(), smem);
     });
     return e == cudaSuccess && n > 0 ? n : 1;
 }
@@ -140,13 +145,13 @@ void launch_sweep2_16(const KParams& p, float* dst, const float* fields, const F
                       cudaStream_t s) {
     const int tx = sh.bx - 4;
     dim3 grid((p.nx + tx - 1) / tx, (p.ny + sh.seg - 1) / sh.seg);
-    const size_t smem = sweep2_16_smem_bytes(sh.bx, sh.cpt, p.coupled);
-    with_shape16(sh.bx, sh.cpt, st, [&](auto B, auto C, auto S) {
+    const size_t smem = sweep2_16_smem_bytes(sh.bx, sh.cpt, sh.out, p.coupled);
+    with_shape16(sh.bx, sh.cpt, st, sh.out, [&](auto B, auto C, auto S, auto O) {
         if (p.coupled)
-            k_sweep2<B(), C(), true, S(), OUT_STAGED><<<grid, 2 * B() / C(), smem, s>>>(
+            k_sweep2<B(), C(), true, S(), O()><<<grid, 2 * B() / C(), smem, s>>>(
                 load_map, store_maps, p, dst, fields, sh.seg, err);
         else
-            k_sweep2<B(), C(), false, S(), OUT_STAGED><<<grid, 2 * B() / C(), smem, s>>>(
+            k_sweep2<B(), C(), false, S(), O()><<<grid, 2 * B() / C(), smem, s>>>(
                 load_map, store_maps, p, dst, fields, sh.seg, err);
         return 0;
     });
