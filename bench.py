@@ -252,6 +252,9 @@ def run_ensemble(args, rank, world, local_rank):
     for r, c in zip(b.runs, cases):
         r.init(c.phi, c.c, c.ux, c.uy)
     if args.tile_x or args.seg_y:
+        if args.batch_form:
+            b.set_form(lbm.LBM_BATCH_CHAINS if args.batch_form == "chains"
+                       else lbm.LBM_BATCH_PERSISTENT)
         b.set_launch_shape(args.tile_x, args.seg_y)
         tuned = None
     else:
@@ -572,6 +575,8 @@ def main():
     ap.add_argument("--kernel", choices=["auto", "tma", "fused", "split"], default="auto")
     ap.add_argument("--tile-x", type=int, default=0)
     ap.add_argument("--seg-y", type=int, default=0)
+    ap.add_argument("--batch-form", choices=["chains", "persistent"], default=None,
+                    help="ensemble with a given launch shape: the batched form (default persistent)")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-budget", type=float, default=90.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
