@@ -25,8 +25,8 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIBDIR = os.path.join(_HERE, "_lib")
 _SO = os.path.join(_LIBDIR, "liblbm_oracle.so")
-_SRC = [os.path.join(_HERE, "lbm_oracle.c")]
-_HDR = os.path.join(_HERE, "lbm_oracle.h")
+_SRC = [os.path.join(_HERE, "lbm_oracle.c"), os.path.join(_HERE, "lbm_oracle3.c")]
+_HDRS = [os.path.join(_HERE, "lbm_oracle.h"), os.path.join(_HERE, "lbm_oracle3.h")]
 _lock = threading.Lock()
 _lib = None
 
@@ -35,7 +35,7 @@ def build(force: bool = False, openmp: bool = True) -> str:
     """Compile the oracle with gcc into oracle/_lib/liblbm_oracle.so."""
     os.makedirs(_LIBDIR, exist_ok=True)
     # the build flags live in this file: a change to it rebuilds too
-    newest = max(os.path.getmtime(p) for p in _SRC + [_HDR, os.path.abspath(__file__)])
+    newest = max(os.path.getmtime(p) for p in _SRC + _HDRS + [os.path.abspath(__file__)])
     if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= newest:
         return _SO
     tmp = _SO + f".tmp{os.getpid()}"
@@ -74,6 +74,14 @@ class OrcDiag(ctypes.Structure):
     ]
 
 
+class Orc3Params(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int), ("pad_", ctypes.c_int),
+        ("W", ctypes.c_double), ("phi_a", ctypes.c_double), ("phi_b", ctypes.c_double),
+        ("M_phi", ctypes.c_double), ("D_s", ctypes.c_double),
+    ]
+
+
 _DP = ctypes.POINTER(ctypes.c_double)
 
 
@@ -103,6 +111,22 @@ def lib():
             L.orc_matrix_Finv.argtypes = [ctypes.c_double, ctypes.c_double, _DP]
             L.orc_gradient.argtypes = [ctypes.c_void_p, _DP, _DP, _DP]
             L.orc_num_threads.restype = ctypes.c_int
+            L.orc3_create.restype = ctypes.c_void_p
+            L.orc3_create.argtypes = [ctypes.POINTER(Orc3Params)]
+            L.orc3_destroy.argtypes = [ctypes.c_void_p]
+            L.orc3_init.argtypes = [ctypes.c_void_p] + [_DP] * 5
+            L.orc3_step.argtypes = [ctypes.c_void_p, ctypes.c_int]
+            L.orc3_get_step.restype = ctypes.c_longlong
+            L.orc3_get_step.argtypes = [ctypes.c_void_p]
+            L.orc3_fields.argtypes = [ctypes.c_void_p, _DP, _DP]
+            L.orc3_normals.argtypes = [ctypes.c_void_p] + [_DP] * 3
+            L.orc3_get_pops.argtypes = [ctypes.c_void_p, _DP, _DP]
+            L.orc3_velocities.argtypes = [ctypes.POINTER(ctypes.c_int)]
+            for name in ("orc3_matrix_P", "orc3_matrix_Pinv"):
+                getattr(L, name).argtypes = [_DP]
+            for name in ("orc3_matrix_F", "orc3_matrix_Finv"):
+                getattr(L, name).argtypes = [ctypes.c_double] * 3 + [_DP]
+            L.orc3_gradient.argtypes = [ctypes.c_void_p] + [_DP] * 4
             _lib = L
     return _lib
 
@@ -226,3 +250,85 @@ def run_case(case, steps=None):
     s.init(case.phi, case.c, case.ux, case.uy, case.P)
     s.step(case.steps if steps is None else steps)
     return s
+
+
+# ---- D3Q27 scalar lattices under a prescribed velocity (lbm_oracle3.c) -----
+
+def matrix3(name, ux=0.0, uy=0.0, uz=0.0):
+    """The 27 x 27 matrices P, P^-1, F(u), F^-1(u) of the 3-D oracle."""
+    out = np.zeros(729)
+    L = lib()
+    if name in ("P", "Pinv"):
+        getattr(L, f"orc3_matrix_{name}")(_ptr(out))
+    elif name in ("F", "Finv"):
+        getattr(L, f"orc3_matrix_{name}")(ux, uy, uz, _ptr(out))
+    else:
+        raise ValueError(name)
+    return out.reshape(27, 27)
+
+
+def velocities3():
+    """The 27 velocities of the 3-D oracle in its population order, [27][3]."""
+    buf = (ctypes.c_int * 81)()
+    lib().orc3_velocities(buf)
+    return np.array(list(buf), dtype=np.int64).reshape(27, 3)
+
+
+class Sim3:
+    """One 3-D oracle run.  Fields are [nz][ny][nx] float64, periodic."""
+
+    def __init__(self, nx, ny, nz, W=4.0, phi_a=1.0, phi_b=0.0, M_phi=0.1, D_s=0.1):
+        self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
+        self._p = Orc3Params(nx=self.nx, ny=self.ny, nz=self.nz, W=W, phi_a=phi_a,
+                             phi_b=phi_b, M_phi=M_phi, D_s=D_s)
+        self._h = lib().orc3_create(ctypes.byref(self._p))
+        if not self._h:
+            raise ValueError("oracle: invalid 3-D parameters")
+
+    @property
+    def shape(self):
+        return (self.nz, self.ny, self.nx)
+
+    def close(self):
+        if self._h:
+            lib().orc3_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init(self, phi, c, ux=0.0, uy=0.0, uz=0.0):
+        u = [np.broadcast_to(np.asarray(v, dtype=np.float64), self.shape) for v in (ux, uy, uz)]
+        a = [_arr(v) for v in (phi, c, *u)]
+        lib().orc3_init(self._h, *[_ptr(v) for v in a])
+
+    def step(self, n=1):
+        lib().orc3_step(self._h, int(n))
+
+    @property
+    def t(self):
+        return lib().orc3_get_step(self._h)
+
+    def fields(self):
+        phi, c = np.zeros(self.shape), np.zeros(self.shape)
+        lib().orc3_fields(self._h, _ptr(phi), _ptr(c))
+        return {"phi": phi, "c": c}
+
+    def normals(self):
+        out = [np.zeros(self.shape) for _ in range(3)]
+        lib().orc3_normals(self._h, *[_ptr(v) for v in out])
+        return out
+
+    def pops(self):
+        f, h = np.zeros((27,) + self.shape), np.zeros((27,) + self.shape)
+        lib().orc3_get_pops(self._h, _ptr(f), _ptr(h))
+        return {"f": f, "h": h}
+
+    def gradient(self, field):
+        a = _arr(field)
+        g = [np.zeros_like(a) for _ in range(3)]
+        lib().orc3_gradient(self._h, _ptr(a), *[_ptr(v) for v in g])
+        return g

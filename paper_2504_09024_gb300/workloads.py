@@ -231,3 +231,74 @@ def lively_shear_drop(nx=100, ny=60, R=14.0, W=4.0, steps=400) -> Case:
                          c_of_theta=lambda t: 0.3 + 0.15 * np.cos(t) + 0.05 * np.sin(2 * t))
     ux, uy = shear_profile(nx, ny, U)
     return Case("lively_shear_drop", phys, phi, c, ux, uy, None, steps)
+
+
+# ---- three-dimensional workloads (D3Q27 scalar lattices, prescribed u) -----
+
+@dataclasses.dataclass
+class Case3:
+    """A 3-D run of the two scalar lattices under a prescribed velocity.
+
+    Fields are [nz][ny][nx] float64 (x fastest), periodic on every axis; the
+    velocity is either three constants or three fields of that shape.
+    """
+    name: str
+    nx: int
+    ny: int
+    nz: int
+    W: float
+    M_phi: float
+    D_s: float
+    phi: np.ndarray
+    c: np.ndarray
+    u: tuple
+    steps: int
+    phi_a: float = 1.0
+    phi_b: float = 0.0
+    meta: dict = dataclasses.field(default_factory=dict)
+
+
+def cell_centres3(nx: int, ny: int, nz: int):
+    """Cell centres (i + 1/2, j + 1/2, k + 1/2) as three [nz][ny][nx] arrays."""
+    z, y, x = np.meshgrid(np.arange(nz) + 0.5, np.arange(ny) + 0.5, np.arange(nx) + 0.5,
+                          indexing="ij")
+    return x, y, z
+
+
+def sphere_fields(nx, ny, nz, R, W, centre=None, phi_a=1.0, phi_b=0.0,
+                  c_of_cos=None, c0=0.0):
+    """Spherical drop: tanh phase profile and sech^2 surfactant band.
+
+    c_of_cos(mu) gives c_hat on the interface as a function of the polar
+    cosine mu = (z - z_o) / |x - x_o| (axis along z); if None, c_hat = c0.
+    """
+    if centre is None:
+        centre = (nx / 2.0, ny / 2.0, nz / 2.0)
+    X, Y, Z = cell_centres3(nx, ny, nz)
+    dx, dy, dz = X - centre[0], Y - centre[1], Z - centre[2]
+    r = np.sqrt(dx * dx + dy * dy + dz * dz)
+    zeta = R - r
+    phi_m = 0.5 * (phi_a + phi_b)
+    phi_o = 0.5 * (phi_a - phi_b)
+    phi = phi_m + phi_o * np.tanh(2.0 * zeta / W)
+    mu = np.where(r > 0.0, dz / np.maximum(r, 1e-300), 0.0)
+    chat = c_of_cos(mu) if c_of_cos is not None else np.full_like(r, c0)
+    c = chat / np.cosh(np.clip(2.0 * zeta / W, -300.0, 300.0)) ** 2
+    return phi, c
+
+
+def sphere_surface_mode(n=256, R=None, W=4.0, D_s=0.1, M_phi=0.1, mode=1, amp=0.1,
+                        base=0.5, u=(0.0, 0.0, 0.0), steps=None) -> Case3:
+    """A spherical drop of radius R in an n^3 periodic box carrying the surface
+    mode c_hat = base + amp P_l(mu) (l = 1 or 2) of its surfactant: the 3-D
+    form of the static drop of Sec. 4.1; with u != 0 the drop is advected as in
+    the second case of Sec. 4.1.  The default length is one e-folding time of
+    the mode, R^2 / (l (l + 1) D_s)."""
+    if R is None:
+        R = n / 4.0
+    legendre = {1: lambda m: m, 2: lambda m: 0.5 * (3.0 * m * m - 1.0)}[mode]
+    phi, c = sphere_fields(n, n, n, R, W, c_of_cos=lambda m: base + amp * legendre(m))
+    if steps is None:
+        steps = int(round(R * R / (mode * (mode + 1) * D_s)))
+    return Case3(f"sphere_{n}^3_l{mode}", n, n, n, W, M_phi, D_s, phi, c, tuple(u), steps,
+                 meta=dict(R=R, mode=mode, amp=amp, base=base))
