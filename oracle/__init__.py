@@ -121,6 +121,7 @@ def lib():
             L.orc3_fields.argtypes = [ctypes.c_void_p, _DP, _DP]
             L.orc3_normals.argtypes = [ctypes.c_void_p] + [_DP] * 3
             L.orc3_get_pops.argtypes = [ctypes.c_void_p, _DP, _DP]
+            L.orc3_set_pops.argtypes = [ctypes.c_void_p, _DP, _DP]
             L.orc3_velocities.argtypes = [ctypes.POINTER(ctypes.c_int)]
             for name in ("orc3_matrix_P", "orc3_matrix_Pinv"):
                 getattr(L, name).argtypes = [_DP]
@@ -326,6 +327,10 @@ class Sim3:
         f, h = np.zeros((27,) + self.shape), np.zeros((27,) + self.shape)
         lib().orc3_get_pops(self._h, _ptr(f), _ptr(h))
         return {"f": f, "h": h}
+
+    def set_pops(self, f=None, h=None):
+        a = [_arr(v) for v in (f, h)]
+        lib().orc3_set_pops(self._h, *[_ptr(v) for v in a])
 
     def gradient(self, field):
         a = _arr(field)

@@ -455,3 +455,9 @@ void orc3_get_pops(const orc3_sim *s, double *f, double *h) {
     if (f) memcpy(f, s->f, bytes);
     if (h) memcpy(h, s->h, bytes);
 }
+
+void orc3_set_pops(orc3_sim *s, const double *f, const double *h) {
+    size_t bytes = sizeof(double) * Q3 * (size_t)s->N;
+    if (f) memcpy(s->f, f, bytes);
+    if (h) memcpy(s->h, h, bytes);
+}

@@ -43,6 +43,8 @@ void orc3_fields(orc3_sim *s, double *phi, double *c);
 /* Unit normal of the current phi (components may be NULL). */
 void orc3_normals(orc3_sim *s, double *nx_, double *ny_, double *nz_);
 void orc3_get_pops(const orc3_sim *s, double *f, double *h);
+/* Replace the post-streaming populations (NULL leaves that lattice unchanged). */
+void orc3_set_pops(orc3_sim *s, const double *f, const double *h);
 /* The 27 velocities, e[3 * a + axis]. */
 void orc3_velocities(int out[81]);
 /* Building blocks, exposed for the pins: the 27 x 27 matrices, row-major. */

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "_lib")
 SO = os.path.join(LIBDIR, "liblbm.so")
 SOURCES = ["lbm_kernels.cu", "lbm_sweep_tma.cu", "lbm_sweep_tma16.cu", "lbm_api.cu", "lbm_noalloc.cu",
-           "surr_mlp.cu"]
+           "surr_mlp.cu", "lbm3d.cu"]
 HEADERS = ["lbm_device.cuh", "lbm_internal.h", "lbm_cell.cuh", "lbm_tma.cuh", "lbm_sweep2.cuh",
            "lbm_store16.cuh", "lbm_vec.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -35,6 +35,7 @@ def nvcc() -> str:
 def _newest_input() -> float:
     files = [os.path.join(CSRC, f) for f in SOURCES + HEADERS]
     files.append(os.path.join(ROOT, "include", "lbm.h"))
+    files.append(os.path.join(ROOT, "include", "lbm3.h"))
     files.append(os.path.abspath(__file__))
     return max(os.path.getmtime(f) for f in files)
 
@@ -84,4 +85,5 @@ def source_hash() -> str:
     for f in sorted(SOURCES + HEADERS):
         h.update(open(os.path.join(CSRC, f), "rb").read())
     h.update(open(os.path.join(ROOT, "include", "lbm.h"), "rb").read())
+    h.update(open(os.path.join(ROOT, "include", "lbm3.h"), "rb").read())
     return h.hexdigest()[:16]
