@@ -8,6 +8,9 @@ exceed L2, so no explicit flush is needed between steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
+--workload sphere3d (sphere3d-384) times the D3Q27 phase-field + surfactant
+step on a 256^3 (384^3) advected spherical drop instead.
+
 --impl reference times the FP64 CPU oracle on the host cores instead (each
 step a bounded window of the same workload).  Under torchrun (N > 1) every
 rank runs an independent replica (the single-grid path has no exchange step);
@@ -135,7 +138,7 @@ def traffic_record(kernel_name):
     if not rec:
         return None
     from paper_2504_09024_gb300 import build as B
-    if rec.get("source_hash") != B.source_hash():
+    if rec.get("source_hash") != B.source_hash("3d" if kernel_name.startswith("k3_") else "2d"):
         return None
     return rec
 
@@ -472,6 +475,133 @@ def ensemble_comparison(args, stream):
             "timing": f"median of 3 regions of {k} steps, CUDA events"}
 
 
+# The D3Q27 phase-field + surfactant step (include/lbm3.h): 27 fixed-point
+# words per lattice read and written once per cell update, two lattices.
+BYTES_PER_CELL_3D = 432
+SPHERE3D_N = {"sphere3d": 256, "sphere3d-384": 384,
+              "sphere3d-128": 128}  # 128^3 (0.9 GB, above L2): the profiler's small case
+
+
+def sphere3d_case(n):
+    """Spherical drop R = n/4 in an n^3 periodic box with an l = 1 surface
+    mode of surfactant, advected by a uniform velocity (the 3-D form of the
+    advected drop of Sec. 4.1)."""
+    from paper_2504_09024_gb300 import workloads as W
+    return W.sphere_surface_mode(n=n, W=4.0, D_s=0.1, M_phi=0.05, mode=1, u=(0.02, -0.013, 0.009))
+
+
+def cpu_baseline_3d(budget_s=15.0):
+    """The 3-D FP64 oracle on the host cores: the same workload scaled down to
+    a 32^3 box (R = 8), as many steps as fit the budget."""
+    import oracle
+    case = sphere3d_case(32)
+    s = oracle.Sim3(32, 32, 32, W=case.W, M_phi=case.M_phi, D_s=case.D_s)
+    s.init(case.phi, case.c, *case.u)
+    t0 = time.perf_counter()
+    s.step(2)
+    per_step = (time.perf_counter() - t0) / 2
+    steps = max(1, int(budget_s / per_step))
+    t0 = time.perf_counter()
+    s.step(steps)
+    dt = time.perf_counter() - t0
+    s.close()
+    return {"value": 32 ** 3 * steps / dt / 1e6, "unit": UNIT, "cores": oracle.num_threads(),
+            "kind": "oracle", "sample": f"{steps} steps of the same workload scaled to a 32^3 box "
+                                        f"(R = 8), {dt:.1f} s"}
+
+
+def bench_sphere3d(n, args, stream, dist=None):
+    """Autotuned 3-D context on the n^3 sphere: W warm-up steps and one untimed
+    pass of K, then `repeats` timed regions of K steps (CUDA events on the
+    library's stream), and the end-to-end leg through the public API."""
+    import torch
+    from paper_2504_09024_gb300 import lbm3
+    case = sphere3d_case(n)
+    g = lbm3.Sim3(n, n, n, W=case.W, M_phi=case.M_phi, D_s=case.D_s, u=case.u,
+                  stream=stream.cuda_stream)
+    if args.rows or args.seg_z:
+        lbm3.lbm3_set_launch_shape(g.ctx, args.rows, args.seg_z)
+        rows, seg = lbm3.lbm3_get_launch_shape(g.ctx)
+    else:
+        rows, seg, tms = lbm3.lbm3_autotune(g.ctx, 8)
+    host_in = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in (case.phi, case.c)]
+    lbm3.lbm3_init_fields(g.ctx, *[a.numpy() for a in host_in])
+    g.step(args.warmup)
+    g.step(args.steps)
+    g.synchronize()
+    times = timed_regions(g.step, stream, args.steps, args.repeats, dist)
+    ms_step = statistics.median(times) / args.steps
+    host_out = [torch.empty((n, n, n), dtype=torch.float64).pin_memory() for _ in range(2)]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lbm3.lbm3_init_fields(g.ctx, *[a.numpy() for a in host_in])
+    g.step(args.steps)
+    lbm3.lbm3_get_fields(g.ctx, *[a.numpy() for a in host_out])
+    sums = g.sums()
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dist)
+    peak, peak_kind = peaks()
+    achieved = BYTES_PER_CELL_3D * n ** 3 / (ms_step * 1e-3) / 1e9
+    tr = traffic_record("k3_step")
+    out = {
+        "case": case, "ms_step": ms_step, "times": times, "e2e_s": e2e_s,
+        "h2d": sum(a.numel() * 8 for a in host_in), "d2h": sum(a.numel() * 8 for a in host_out) + 24,
+        "launch_shape": [rows, seg], "sums": sums,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_kind": f"{peak_kind} hbm_gbs",
+                     "bytes_per_cell": BYTES_PER_CELL_3D,
+                     "traffic": tr["bytes_per_launch"] if tr else None},
+    }
+    g.close()
+    return out
+
+
+def run_sphere3d(args, rank, world, local_rank):
+    import torch
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist  # noqa: F811
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    n = SPHERE3D_N[args.workload]
+    stream = torch.cuda.Stream()
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    time.sleep(0.3)
+    r = bench_sphere3d(n, args, stream, dist)
+    clk = clocks.stop()
+    ncell = n ** 3
+    line = {
+        "metric": "D3Q27 phase-field + surfactant MLUPS", "value": whole_job_mlups(world, ncell, args.steps, r["ms_step"] * args.steps * 1e-3),
+        "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": r["ms_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "fixed-point int32 storage, f32 arithmetic", "data": "synthetic",
+        "config": {"workload": r["case"].name, "grid": f"{n}x{n}x{n}", "cells": ncell,
+                   "lattices": "f+h (D3Q27) under a uniform prescribed velocity",
+                   "kernel": "k3_step", "launch_shape": r["launch_shape"],
+                   "launch_shape_from": "command line" if (args.rows or args.seg_z) else "lbm3_autotune",
+                   "timed_regions": f"median of {args.repeats} regions of {args.steps} steps",
+                   "l2": f"populations (2 x {ncell * 216 / 1e9:.1f} GB) exceed the 129 MB L2; no flush",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "roofline": r["roofline"],
+        "e2e": {"value": whole_job_mlups(world, ncell, args.steps, r["e2e_s"]), "unit": UNIT,
+                "h2d_bytes_per_step": r["h2d"] / args.steps, "d2h_bytes_per_step": r["d2h"] / args.steps,
+                "what": "lbm3_init_fields from pinned host fields + lbm3_step(K) + lbm3_get_fields "
+                        "to pinned host + lbm3_sums"},
+        "gpu_launches": args.steps,
+        "clocks": clk,
+        "check": {"sum_phi": r["sums"]["sum_phi"], "sum_c": r["sums"]["sum_c"],
+                  "invalid": r["sums"]["nonfinite"]},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_3d(args.cpu_budget)
+    if rank == 0:
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     from paper_2504_09024_gb300 import lbm
@@ -555,6 +685,12 @@ def run_ours(args, rank, world, local_rank):
                         "roofline": roofline(dt, ncell, ms16, "k_sweep2_16")}
             s16.close()
         line["ensemble64"] = ensemble_comparison(args, stream)
+        r3 = bench_sphere3d(256, args, stream)
+        line["sphere3d"] = {"workload": r3["case"].name, "value": 256 ** 3 / (r3["ms_step"] * 1e-3) / 1e6,
+                            "unit": UNIT, "ms_per_step": r3["ms_step"],
+                            "launch_shape": r3["launch_shape"], "roofline": r3["roofline"],
+                            "what": "D3Q27 phase-field + surfactant lattices, fixed-point storage, "
+                                    "uniform prescribed velocity (k3_step, one launch per step)"}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(case, args.cpu_budget)
     if rank == 0:
@@ -575,6 +711,8 @@ def main():
     ap.add_argument("--kernel", choices=["auto", "tma", "fused", "split"], default="auto")
     ap.add_argument("--tile-x", type=int, default=0)
     ap.add_argument("--seg-y", type=int, default=0)
+    ap.add_argument("--rows", type=int, default=0, help="3-D workloads: tile rows (6, 10, 18)")
+    ap.add_argument("--seg-z", type=int, default=0, help="3-D workloads: planes per block")
     ap.add_argument("--batch-form", choices=["chains", "persistent"], default=None,
                     help="ensemble with a given launch shape: the batched form (default persistent)")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
@@ -594,6 +732,8 @@ def main():
         return run_reference(args, rank, world)
     if args.workload.startswith("ensemble"):
         return run_ensemble(args, rank, world, local_rank)
+    if args.workload in SPHERE3D_N:
+        return run_sphere3d(args, rank, world, local_rank)
     return run_ours(args, rank, world, local_rank)
 
 

@@ -133,7 +133,7 @@ int lbm3_set_launch_shape(lbm3_ctx *ctx, int32_t rows, int32_t seg_z);
 int lbm3_get_launch_shape(const lbm3_ctx *ctx, int32_t *rows, int32_t *seg_z);
 
 /* Time `steps` steps (CUDA events, after one warm-up step) for each
- * candidate shape (rows in {6, 10, 18} x seg_z in {16, 32, 64, 128, nz}),
+ * candidate shape (rows in {6, 10, 18} x seg_z in {4, 8, 16, 32, 64, nz}),
  * keep the fastest and report it (outputs may be NULL).  Advances the state
  * by the steps it timed; call it before lbm3_init_fields.  Synchronous. */
 int lbm3_autotune(lbm3_ctx *ctx, int32_t steps, int32_t *rows, int32_t *seg_z, double *ms_per_step);

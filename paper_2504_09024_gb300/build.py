@@ -78,12 +78,21 @@ if __name__ == "__main__":
     print(build(force=True, verbose=True))
 
 
-def source_hash() -> str:
-    """Hash of the CUDA sources and the ABI header (keys profiler records)."""
+SOURCES_3D = ["lbm3d.cu"]
+
+
+def source_hash(which: str = "2d") -> str:
+    """Hash of the sources of one kernel family, keying profiler records:
+    "2d" -- the coupled D2Q9 sweeps, their headers and include/lbm.h;
+    "3d" -- the D3Q27 step (lbm3d.cu) and include/lbm3.h."""
     import hashlib
     h = hashlib.sha256()
-    for f in sorted(SOURCES + HEADERS):
+    if which == "3d":
+        for f in SOURCES_3D:
+            h.update(open(os.path.join(CSRC, f), "rb").read())
+        h.update(open(os.path.join(ROOT, "include", "lbm3.h"), "rb").read())
+        return h.hexdigest()[:16]
+    for f in sorted([f for f in SOURCES if f not in SOURCES_3D] + HEADERS):
         h.update(open(os.path.join(CSRC, f), "rb").read())
     h.update(open(os.path.join(ROOT, "include", "lbm.h"), "rb").read())
-    h.update(open(os.path.join(ROOT, "include", "lbm3.h"), "rb").read())
     return h.hexdigest()[:16]

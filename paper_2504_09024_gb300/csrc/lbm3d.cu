@@ -31,10 +31,14 @@
 // Step kernel.  A block owns a 30 x (ROWS - 2) column tile with a one-cell
 // halo (one warp per row of 32 columns) and marches through seg_z planes.
 // At plane k it pulls the f populations of plane k + 1 for every tile and
-// halo cell (phi into a three-plane shared ring, the first moments of the
-// tile cells kept in registers for the next plane), then updates the tile
+// halo cell (phi into a four-plane shared ring, the first moments of the
+// tile cells kept in registers for the next plane) and the h populations of
+// plane k for the tile cells, waits at one barrier, then updates the tile
 // cells of plane k: gradient of phi from the ring, normal, theta, theta_c,
-// the h pull, both collisions, 54 coalesced stores.
+// both collisions, 54 coalesced stores.  With four ring slots the slot
+// written at plane k + 1 is one no thread still reads, and the one written at
+// plane k + 2 was last read before the barrier of plane k + 1, so one barrier
+// per plane suffices.
 #include <cuda_runtime.h>
 #include <nvtx3/nvToolsExt.h>
 
@@ -166,15 +170,16 @@ __device__ __forceinline__ void store_collision(int* __restrict__ o, long long N
 }
 
 // Resident blocks per SM the register budget is sized for: 96 registers a
-// thread (80 spill).
+// thread at 10 and 18 rows, 80 at 6 rows (four blocks; 12 bytes of spill
+// measured faster than three blocks at 96).
 template <int ROWS>
-constexpr int k3_min_blocks() { return ROWS == 6 ? 3 : ROWS == 10 ? 2 : 1; }
+constexpr int k3_min_blocks() { return ROWS == 6 ? 4 : ROWS == 10 ? 2 : 1; }
 
 template <int ROWS, bool UFIELD>
 __global__ void __launch_bounds__(ROWS * 32, k3_min_blocks<ROWS>()) k3_step(const K3Params p, const int* __restrict__ fa,
                                                      const int* __restrict__ ha, int* __restrict__ fb,
                                                      int* __restrict__ hb) {
-    __shared__ float ring[3][ROWS][TILE_W];
+    __shared__ float ring[4][ROWS][TILE_W];
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     const int gx = blockIdx.x * TILE_IN + tx - 1;
     const int gy = blockIdx.y * (ROWS - 2) + ty - 1;
@@ -194,7 +199,7 @@ __global__ void __launch_bounds__(ROWS * 32, k3_min_blocks<ROWS>()) k3_step(cons
         zs[2] = (long long)wrapi(z + 1, p.nz) * nxny;
     };
 
-    int sm = 0, sc = 1, sp = 2;  // ring slots of planes k - 1, k, k + 1
+    int sm = 0, sc = 1, sp = 2, sf = 3;  // ring slots of planes k - 1, k, k + 1 (sf: free)
     long long zs[3];
     planes(wrapi(z0 - 1, p.nz), zs);
     ring[sm][ty][tx] = fx_to_f(pull_moments(fa, N, zs, ys, xs).s);
@@ -210,28 +215,28 @@ __global__ void __launch_bounds__(ROWS * 32, k3_min_blocks<ROWS>()) k3_step(cons
         planes(wrapi(k + 1, p.nz), zs);
         const Moments nxt = pull_moments(fa, N, zs, ys, xs);
         ring[sp][ty][tx] = fx_to_f(nxt.s);
+        Moments hm{0u, 0u, 0u, 0u};
+        if (inner) hm = pull_moments(ha, N, zc, ys, xs);
         __syncthreads();
         if (inner) {
-            // gradient d_i phi = (1/cs2) sum_a w_a e_ai phi(x + e_a)
-            float P[3][3][3];  // [dz][dy][dx], offsets -1, 0, +1
-#pragma unroll
-            for (int dy = 0; dy < 3; ++dy)
-#pragma unroll
-                for (int dx = 0; dx < 3; ++dx) {
-                    P[0][dy][dx] = ring[sm][ty + dy - 1][tx + dx - 1];
-                    P[1][dy][dx] = ring[sc][ty + dy - 1][tx + dx - 1];
-                    P[2][dy][dx] = ring[sp][ty + dy - 1][tx + dx - 1];
-                }
+            // gradient d_i phi = (1/cs2) sum_a w_a e_ai phi(x + e_a), accumulated
+            // value by value from the ring (weights (1/2) w1 w1 on the two
+            // transverse offsets)
             float gxv = 0.f, gyv = 0.f, gzv = 0.f;
 #pragma unroll
-            for (int i = 0; i < 3; ++i)
+            for (int dz = 0; dz < 3; ++dz) {
+                const float(*plane)[TILE_W] = ring[dz == 0 ? sm : dz == 1 ? sc : sp];
 #pragma unroll
-                for (int j = 0; j < 3; ++j) {
-                    const float w = w1[i] * w1[j];
-                    gxv += w * (P[i][j][2] - P[i][j][0]);
-                    gyv += w * (P[i][2][j] - P[i][0][j]);
-                    gzv += w * (P[2][i][j] - P[0][i][j]);
-                }
+                for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+                    for (int dx = 0; dx < 3; ++dx) {
+                        if (dx == 1 && dy == 1 && dz == 1) continue;
+                        const float v = plane[ty + dy - 1][tx + dx - 1];
+                        if (dx != 1) gxv += (dx == 2 ? w1[dy] * w1[dz] : -w1[dy] * w1[dz]) * v;
+                        if (dy != 1) gyv += (dy == 2 ? w1[dx] * w1[dz] : -w1[dx] * w1[dz]) * v;
+                        if (dz != 1) gzv += (dz == 2 ? w1[dx] * w1[dy] : -w1[dx] * w1[dy]) * v;
+                    }
+            }
             gxv *= 0.5f;
             gyv *= 0.5f;
             gzv *= 0.5f;
@@ -239,7 +244,6 @@ __global__ void __launch_bounds__(ROWS * 32, k3_min_blocks<ROWS>()) k3_step(cons
             const float inv = g2 > 1e-24f ? rsqrtf(g2) : 0.f;
             const float n3[3] = {gxv * inv, gyv * inv, gzv * inv};
 
-            const Moments hm = pull_moments(ha, N, zc, ys, xs);
             const long long cell = zc[0] + ys[0] + x;
             // velocity factors: from the parameters (uniform u) or per cell
             float u3[3] = {p.u[0], p.u[1], p.u[2]};
@@ -275,11 +279,11 @@ __global__ void __launch_bounds__(ROWS * 32, k3_min_blocks<ROWS>()) k3_step(cons
             store_collision(fb + cell, N, ok, cur.s, Ax, Bx, Cx, Ay, By, Cy, Az, Bz, Cz, phi, kf);
             store_collision(hb + cell, N, ok, hm.s, Ax, Bx, Cx, Ay, By, Cy, Az, Bz, Cz, c, kh);
         }
-        __syncthreads();
         const int t = sm;
         sm = sc;
         sc = sp;
-        sp = t;
+        sp = sf;
+        sf = t;
         cur = nxt;
 #pragma unroll
         for (int i = 0; i < 3; ++i) zc[i] = zs[i];
@@ -765,7 +769,7 @@ int lbm3_autotune(lbm3_ctx* ctx, int32_t steps, int32_t* rows_out, int32_t* seg_
     const int nz = ctx->kp.nz;
     const int row_c[3] = {6, 10, 18};
     std::vector<int> segs;
-    for (int s : {16, 32, 64, 128, nz}) {
+    for (int s : {4, 8, 16, 32, 64, nz}) {
         const int v = s < nz ? s : nz;
         bool seen = false;
         for (int t : segs) seen = seen || t == v;
