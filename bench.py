@@ -178,11 +178,54 @@ def cpu_baseline(case, budget_s=15.0):
                       f"workload through the drop interface ({dt:.1f} s)"}
 
 
+def run_reference_3d(args, world):
+    """The 3-D oracle on the host cores: the sphere workload scaled down to a
+    box whose (warm-up + timed) steps fit the budget."""
+    import oracle
+    n_full = SPHERE3D_N[args.workload]
+    probe = sphere3d_case(16)
+    s = oracle.Sim3(16, 16, 16, W=probe.W, M_phi=probe.M_phi, D_s=probe.D_s)
+    s.init(probe.phi, probe.c, *probe.u)
+    s.step(1)
+    t0 = time.perf_counter()
+    s.step(3)
+    t_cell = (time.perf_counter() - t0) / (3 * 16 ** 3)
+    s.close()
+    total_steps = args.steps + args.warmup
+    n = int((args.ref_budget / (total_steps * t_cell)) ** (1.0 / 3.0))
+    n = max(8, min(n_full, n - n % 4))
+    case = sphere3d_case(n)
+    s = oracle.Sim3(n, n, n, W=case.W, M_phi=case.M_phi, D_s=case.D_s)
+    s.init(case.phi, case.c, *case.u)
+    s.step(args.warmup)
+    t0 = time.perf_counter()
+    s.step(args.steps)
+    dt = time.perf_counter() - t0
+    s.close()
+    value = n ** 3 * args.steps / dt / 1e6
+    line = {
+        "impl": "reference", "metric": "D3Q27 phase-field + surfactant MLUPS", "value": value,
+        "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"sphere_{n_full}^3_l1",
+                   "grid": f"{n_full}x{n_full}x{n_full}", "sample": f"the same drop scaled to {n}^3",
+                   "parallelism": "host threads"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                         "sample": f"each step: one oracle step of the workload scaled to {n}^3"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
     import oracle
     oracle.build()
+    if args.workload in SPHERE3D_N:
+        return run_reference_3d(args, world)
     case = make_case(args.workload)
     from paper_2504_09024_gb300 import workloads as W
     nx, ny = case.phys.nx, case.phys.ny
