@@ -28,7 +28,8 @@
  *     velocity (E[a % 3], E[(a / 3) % 3], E[a / 9]) with E = {0, +1, -1};
  *     lbm3_velocities() returns the list.
  *   - Populations are stored on the device as int32 fixed point in units of
- *     2^-28 (range +-8), two buffers of 2 x 27 x nx ny nz words (ping-pong);
+ *     2^-28 (range +-8), plane by plane ([nz][27][ny][nx] words per lattice),
+ *     two buffers of 2 x 27 x nx ny nz words (ping-pong);
  *     the collision arithmetic is FP32.  The pull sums are exact integer sums
  *     and each collision gives its rest population the integer remainder of
  *     the cell's zeroth moment, so sum phi and sum c are conserved exactly.
@@ -50,7 +51,8 @@ extern "C" {
 #endif
 
 /* nx * ny * nz may not exceed this (populations of 2^31 cells would need
- * 464 GB; 2^30 cells need 232 GB of the GPU's memory). */
+ * 464 GB; 2^30 cells need 232 GB of the GPU's memory), and 27 * nx * ny must
+ * stay below 2^31 (offsets inside a plane's 27 populations are 32-bit). */
 #define LBM3_MAX_CELLS 1073741824LL
 
 typedef struct lbm3_params {
@@ -71,7 +73,7 @@ int lbm3_params_default(lbm3_params *p);
 /* Validate *p and create a context on the current CUDA device.
  * stream: a cudaStream_t or NULL.  Allocates the two population buffers, the
  * velocity field (velocity_field = 1) and reduction scratch.
- * Errors: INVALID_ARG (NULL, a size < 1, too many cells, phi_a == phi_b,
+ * Errors: INVALID_ARG (NULL, a size < 1, too many cells, 27 nx ny >= 2^31, phi_a == phi_b,
  * |phi_a| or |phi_b| > 2, a uniform |u_i| >= 1/2, W <= 0, a non-finite
  * value), RATE (M_phi or D_s <= 0), NOMEM, CUDA. */
 int lbm3_create(const lbm3_params *p, void *stream, lbm3_ctx **out);

@@ -19,7 +19,9 @@
 // populations: the pull loads are summed as they arrive.
 //
 // Storage in fixed point.  Populations are int32 in units of 2^-28 (range
-// +-8).  The pull sums are exact integer sums; the collision runs in FP32 on
+// +-8), plane by plane: word (z, q, y, x) of a lattice is at
+// ((z * 27 + q) * ny + y) * nx + x, so every offset inside a plane's 27
+// populations fits 32 bits (27 nx ny < 2^31) and only the plane base is 64-bit.  The pull sums are exact integer sums; the collision runs in FP32 on
 // those moments, its 26 moving outputs are rounded to the grid, and the rest
 // population takes the integer remainder s - sum(others), so every collision
 // conserves sum f and sum h exactly.  (With FP32 storage every cell of a
@@ -126,18 +128,20 @@ struct Moments {
     uint32_t s, jx, jy, jz;
 };
 
-__device__ __forceinline__ Moments pull_moments(const int* __restrict__ base, long long N,
-                                                const long long (&zs)[3], const long long (&ys)[3],
-                                                const int (&xs)[3]) {
+__device__ __forceinline__ Moments pull_moments(const int* __restrict__ base, long long pstride, int nxny,
+                                                const int (&zs)[3], const int (&ys)[3], const int (&xs)[3]) {
     Moments m{0u, 0u, 0u, 0u};
+    const int x1 = nxny + xs[1], x2 = 2 * nxny + xs[2];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
+        const int* q0 = base + zs[c] * pstride + 9 * c * nxny;  // population (0, 0, c) of the plane
 #pragma unroll
         for (int b = 0; b < 3; ++b) {
-            const int* row = base + (9 * c + 3 * b) * N + zs[c] + ys[b];
+            const int* row = q0 + ys[b];
+            q0 += 3 * nxny;
             const uint32_t v0 = (uint32_t)__ldg(row + xs[0]);
-            const uint32_t v1 = (uint32_t)__ldg(row + N + xs[1]);
-            const uint32_t v2 = (uint32_t)__ldg(row + 2 * N + xs[2]);
+            const uint32_t v1 = (uint32_t)__ldg(row + x1);
+            const uint32_t v2 = (uint32_t)__ldg(row + x2);
             const uint32_t sx = v0 + v1 + v2;
             m.s += sx;
             m.jx += v1 - v2;
@@ -154,7 +158,7 @@ __device__ __forceinline__ float fx_to_f(uint32_t v) { return (float)(int)v * FX
 
 // Round the 26 moving outputs to the grid and give the rest population the
 // remainder of the exact zeroth moment s_fx (or FX_BAD everywhere).
-__device__ __forceinline__ void store_collision(int* __restrict__ o, long long N, bool ok, uint32_t s_fx,
+__device__ __forceinline__ void store_collision(int* __restrict__ o, int nxny, bool ok, uint32_t s_fx,
                                                 const float (&Ax)[3], const float (&Bx)[3], const float (&Cx)[3],
                                                 const float (&Ay)[3], const float (&By)[3], const float (&Cy)[3],
                                                 const float (&Az)[3], const float (&Bz)[3], const float (&Cz)[3],
@@ -164,14 +168,15 @@ __device__ __forceinline__ void store_collision(int* __restrict__ o, long long N
         if (q == 0) return;
         const int iv = ok ? __float2int_rn(v * FX_ONE) : FX_BAD;
         moved += (uint32_t)iv;
-        o[q * N] = iv;
+        o[q * nxny] = iv;
     });
     o[0] = ok ? (int)(s_fx - moved) : FX_BAD;
 }
 
 // Resident blocks per SM the register budget is sized for: 96 registers a
-// thread at 10 and 18 rows, 80 at 6 rows (four blocks; 12 bytes of spill
-// measured faster than three blocks at 96).
+// thread at 10 and 18 rows, 80 at 6 rows (four blocks of six warps; the
+// uniform-velocity variant spills 40 bytes there and is still the fastest
+// shape measured).
 template <int ROWS>
 constexpr int k3_min_blocks() { return ROWS == 6 ? 4 : ROWS == 10 ? 2 : 1; }
 
@@ -187,36 +192,38 @@ __global__ void __launch_bounds__(ROWS * 32, k3_min_blocks<ROWS>()) k3_step(cons
     const int x = wrapi(gx, p.nx), y = wrapi(gy, p.ny);
     // source column / row of the velocity component e = 0, +1, -1
     const int xs[3] = {x, wrapi(gx - 1, p.nx), wrapi(gx + 1, p.nx)};
-    const long long ys[3] = {(long long)y * p.nx, (long long)wrapi(gy - 1, p.ny) * p.nx,
-                             (long long)wrapi(gy + 1, p.ny) * p.nx};
-    const long long N = p.N, nxny = p.nxny;
+    const int ys[3] = {y * p.nx, wrapi(gy - 1, p.ny) * p.nx, wrapi(gy + 1, p.ny) * p.nx};
+    const long long N = p.N;
+    const int nxny = (int)p.nxny;
+    const long long pstride = 27LL * nxny;  // words of one plane's 27 populations
     const int z0 = blockIdx.z * p.seg_z;
     const int z1 = min(p.nz, z0 + p.seg_z);
 
-    auto planes = [&](int z, long long (&zs)[3]) {
-        zs[0] = (long long)z * nxny;
-        zs[1] = (long long)wrapi(z - 1, p.nz) * nxny;
-        zs[2] = (long long)wrapi(z + 1, p.nz) * nxny;
+    // source plane of the velocity component e = 0, +1, -1
+    auto planes = [&](int z, int (&zs)[3]) {
+        zs[0] = z;
+        zs[1] = wrapi(z - 1, p.nz);
+        zs[2] = wrapi(z + 1, p.nz);
     };
 
     int sm = 0, sc = 1, sp = 2, sf = 3;  // ring slots of planes k - 1, k, k + 1 (sf: free)
-    long long zs[3];
+    int zs[3];
     planes(wrapi(z0 - 1, p.nz), zs);
-    ring[sm][ty][tx] = fx_to_f(pull_moments(fa, N, zs, ys, xs).s);
+    ring[sm][ty][tx] = fx_to_f(pull_moments(fa, pstride, nxny, zs, ys, xs).s);
     planes(z0, zs);
-    Moments cur = pull_moments(fa, N, zs, ys, xs);
+    Moments cur = pull_moments(fa, pstride, nxny, zs, ys, xs);
     ring[sc][ty][tx] = fx_to_f(cur.s);
 
     const float w1[3] = {1.0f / 6.0f, 2.0f / 3.0f, 1.0f / 6.0f};  // offsets -1, 0, +1
 
-    long long zc[3];  // planes of the current k (for the h pull)
+    int zc[3];  // planes of the current k (for the h pull)
     planes(z0, zc);
     for (int k = z0; k < z1; ++k) {
         planes(wrapi(k + 1, p.nz), zs);
-        const Moments nxt = pull_moments(fa, N, zs, ys, xs);
+        const Moments nxt = pull_moments(fa, pstride, nxny, zs, ys, xs);
         ring[sp][ty][tx] = fx_to_f(nxt.s);
         Moments hm{0u, 0u, 0u, 0u};
-        if (inner) hm = pull_moments(ha, N, zc, ys, xs);
+        if (inner) hm = pull_moments(ha, pstride, nxny, zc, ys, xs);
         __syncthreads();
         if (inner) {
             // gradient d_i phi = (1/cs2) sum_a w_a e_ai phi(x + e_a), accumulated
@@ -244,7 +251,8 @@ __global__ void __launch_bounds__(ROWS * 32, k3_min_blocks<ROWS>()) k3_step(cons
             const float inv = g2 > 1e-24f ? rsqrtf(g2) : 0.f;
             const float n3[3] = {gxv * inv, gyv * inv, gzv * inv};
 
-            const long long cell = zc[0] + ys[0] + x;
+            const int co = ys[0] + x;                       // offset inside the plane
+            const long long cell = (long long)k * nxny + co;  // cell index (velocity field)
             // velocity factors: from the parameters (uniform u) or per cell
             float u3[3] = {p.u[0], p.u[1], p.u[2]};
             float F[3][3][3];
@@ -276,8 +284,8 @@ __global__ void __launch_bounds__(ROWS * 32, k3_min_blocks<ROWS>()) k3_step(cons
                 kh[i] = b + p.w_chi * (qh * n3[i] - b);
             }
             const bool ok = fabsf(phi) < S_MAX && fabsf(c) < S_MAX;
-            store_collision(fb + cell, N, ok, cur.s, Ax, Bx, Cx, Ay, By, Cy, Az, Bz, Cz, phi, kf);
-            store_collision(hb + cell, N, ok, hm.s, Ax, Bx, Cx, Ay, By, Cy, Az, Bz, Cz, c, kh);
+            store_collision(fb + k * pstride + co, nxny, ok, cur.s, Ax, Bx, Cx, Ay, By, Cy, Az, Bz, Cz, phi, kf);
+            store_collision(hb + k * pstride + co, nxny, ok, hm.s, Ax, Bx, Cx, Ay, By, Cy, Az, Bz, Cz, c, kh);
         }
         const int t = sm;
         sm = sc;
@@ -344,7 +352,7 @@ __global__ void k3_init(const K3Params p, const double* __restrict__ phi, const 
         const int zd[3] = {z, wrapi(z - 1, p.nz), wrapi(z + 1, p.nz)};
         auto dest = [&](int q) {
             const int a = q % 3, b = (q / 3) % 3, cq = q / 9;
-            return q * N + ((long long)zd[cq] * p.ny + yd[b]) * p.nx + xd[a];
+            return ((long long)zd[cq] * Q27 + q) * p.nxny + (long long)yd[b] * p.nx + xd[a];
         };
         const double qf = M_phi * theta, qh = D_s * thetac;
         // non-finite or out-of-range values become FX_BAD
@@ -357,14 +365,15 @@ __global__ void k3_init(const K3Params p, const double* __restrict__ phi, const 
     }
 }
 
-// State of cell x: population a is buffer A's value at x - e_a.
+// State of cell x: population a is buffer A's value at x - e_a (plane-major
+// word index, see the storage note at the top).
 __device__ __forceinline__ long long pull_src(const K3Params& p, long long cell, int q) {
     const int x = (int)(cell % p.nx);
     const int y = (int)((cell / p.nx) % p.ny);
     const int z = (int)(cell / p.nxny);
     const int E[3] = {0, 1, -1};
     const int a = q % 3, b = (q / 3) % 3, c = q / 9;
-    return q * p.N + ((long long)wrapi(z - E[c], p.nz) * p.ny + wrapi(y - E[b], p.ny)) * p.nx +
+    return ((long long)wrapi(z - E[c], p.nz) * Q27 + q) * p.nxny + (long long)wrapi(y - E[b], p.ny) * p.nx +
            wrapi(x - E[a], p.nx);
 }
 
@@ -453,7 +462,7 @@ struct lbm3_ctx {
     K3Params kp;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
-    int* buf[2] = {nullptr, nullptr};    // each: f [27][N] then h [27][N], fixed point
+    int* buf[2] = {nullptr, nullptr};    // each: f [nz][27][ny][nx] then h, fixed point
     float* uf = nullptr;                 // [3][N] prescribed velocity (velocity_field = 1)
     long long* partial = nullptr;        // 3 x SUM_BLOCKS partial sums
     double* result = nullptr;            // 3 totals
@@ -539,6 +548,7 @@ int lbm3_create(const lbm3_params* p, void* stream, lbm3_ctx** out) {
     *out = nullptr;
     if (p->nx < 1 || p->ny < 1 || p->nz < 1) return LBM_ERR_INVALID_ARG;
     if ((long long)p->nx * p->ny * p->nz > LBM3_MAX_CELLS) return LBM_ERR_INVALID_ARG;
+    if (27LL * p->nx * p->ny > 2147483647LL) return LBM_ERR_INVALID_ARG;  // 32-bit in-plane offsets
     if (p->velocity_field != 0 && p->velocity_field != 1) return LBM_ERR_INVALID_ARG;
     const double vals[8] = {p->W, p->phi_a, p->phi_b, p->M_phi, p->D_s, p->u[0], p->u[1], p->u[2]};
     if (!finite_all(vals, 8) || !(p->W > 0.0) || p->phi_a == p->phi_b) return LBM_ERR_INVALID_ARG;

@@ -87,6 +87,7 @@ def _params(**kw):
     (dict(D_s=-0.1), lbm.LBM_ERR_RATE),
     (dict(W=float("nan")), lbm.LBM_ERR_INVALID_ARG),
     (dict(phi_a=2.5), lbm.LBM_ERR_INVALID_ARG),
+    (dict(nx=16384, ny=8192, nz=1), lbm.LBM_ERR_INVALID_ARG),   # 27 nx ny >= 2^31
 ])
 def test_create_rejects_bad_parameters(lib, kw, code):
     h = ctypes.c_void_p()
