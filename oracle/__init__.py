@@ -79,6 +79,12 @@ class Orc3Params(ctypes.Structure):
         ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int), ("pad_", ctypes.c_int),
         ("W", ctypes.c_double), ("phi_a", ctypes.c_double), ("phi_b", ctypes.c_double),
         ("M_phi", ctypes.c_double), ("D_s", ctypes.c_double),
+        ("mode", ctypes.c_int), ("walls_y", ctypes.c_int), ("sigma_literal", ctypes.c_int),
+        ("pad2_", ctypes.c_int),
+        ("u_wall", ctypes.c_double), ("nu_a", ctypes.c_double), ("nu_b", ctypes.c_double),
+        ("zeta", ctypes.c_double), ("rho_a", ctypes.c_double), ("rho_b", ctypes.c_double),
+        ("sigma_o", ctypes.c_double), ("beta", ctypes.c_double), ("c_max", ctypes.c_double),
+        ("fext", ctypes.c_double * 3),
     ]
 
 
@@ -115,6 +121,7 @@ def lib():
             L.orc3_create.argtypes = [ctypes.POINTER(Orc3Params)]
             L.orc3_destroy.argtypes = [ctypes.c_void_p]
             L.orc3_init.argtypes = [ctypes.c_void_p] + [_DP] * 5
+            L.orc3_init_pressure.argtypes = [ctypes.c_void_p] + [_DP] * 6
             L.orc3_step.argtypes = [ctypes.c_void_p, ctypes.c_int]
             L.orc3_get_step.restype = ctypes.c_longlong
             L.orc3_get_step.argtypes = [ctypes.c_void_p]
@@ -128,6 +135,9 @@ def lib():
             for name in ("orc3_matrix_F", "orc3_matrix_Finv"):
                 getattr(L, name).argtypes = [ctypes.c_double] * 3 + [_DP]
             L.orc3_gradient.argtypes = [ctypes.c_void_p] + [_DP] * 4
+            L.orc3_flow_fields.argtypes = [ctypes.c_void_p] + [_DP] * 4
+            L.orc3_get_flow_pops.argtypes = [ctypes.c_void_p, _DP]
+            L.orc3_curvature.argtypes = [ctypes.c_void_p, _DP]
             _lib = L
     return _lib
 
@@ -276,12 +286,22 @@ def velocities3():
 
 
 class Sim3:
-    """One 3-D oracle run.  Fields are [nz][ny][nx] float64, periodic."""
+    """One 3-D oracle run.  Fields are [nz][ny][nx] float64, periodic in x and
+    z, and in y unless walls_y.  flow=True couples the D3Q27 flow lattice
+    (the remaining keywords are its physics, as for the 2-D oracle)."""
 
-    def __init__(self, nx, ny, nz, W=4.0, phi_a=1.0, phi_b=0.0, M_phi=0.1, D_s=0.1):
+    def __init__(self, nx, ny, nz, W=4.0, phi_a=1.0, phi_b=0.0, M_phi=0.1, D_s=0.1,
+                 flow=False, walls_y=0, u_wall=0.0, nu_a=0.1, nu_b=0.1, zeta=1.0 / 6.0,
+                 rho_a=1.0, rho_b=1.0, sigma_o=0.0, beta=0.0, c_max=1.0, fext=(0.0, 0.0, 0.0),
+                 sigma_literal=0):
         self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
         self._p = Orc3Params(nx=self.nx, ny=self.ny, nz=self.nz, W=W, phi_a=phi_a,
-                             phi_b=phi_b, M_phi=M_phi, D_s=D_s)
+                             phi_b=phi_b, M_phi=M_phi, D_s=D_s, mode=1 if flow else 0,
+                             walls_y=int(walls_y), sigma_literal=int(sigma_literal),
+                             u_wall=u_wall, nu_a=nu_a, nu_b=nu_b, zeta=zeta, rho_a=rho_a,
+                             rho_b=rho_b, sigma_o=sigma_o, beta=beta, c_max=c_max)
+        for i in range(3):
+            self._p.fext[i] = float(fext[i])
         self._h = lib().orc3_create(ctypes.byref(self._p))
         if not self._h:
             raise ValueError("oracle: invalid 3-D parameters")
@@ -301,10 +321,14 @@ class Sim3:
         except Exception:
             pass
 
-    def init(self, phi, c, ux=0.0, uy=0.0, uz=0.0):
+    def init(self, phi, c, ux=0.0, uy=0.0, uz=0.0, P=None):
         u = [np.broadcast_to(np.asarray(v, dtype=np.float64), self.shape) for v in (ux, uy, uz)]
         a = [_arr(v) for v in (phi, c, *u)]
-        lib().orc3_init(self._h, *[_ptr(v) for v in a])
+        if P is None:
+            lib().orc3_init(self._h, *[_ptr(v) for v in a])
+        else:
+            Pa = _arr(np.broadcast_to(np.asarray(P, dtype=np.float64), self.shape))
+            lib().orc3_init_pressure(self._h, *[_ptr(v) for v in a], _ptr(Pa))
 
     def step(self, n=1):
         lib().orc3_step(self._h, int(n))
@@ -327,6 +351,21 @@ class Sim3:
         f, h = np.zeros((27,) + self.shape), np.zeros((27,) + self.shape)
         lib().orc3_get_pops(self._h, _ptr(f), _ptr(h))
         return {"f": f, "h": h}
+
+    def flow_fields(self):
+        out = [np.zeros(self.shape) for _ in range(4)]
+        lib().orc3_flow_fields(self._h, *[_ptr(v) for v in out])
+        return dict(zip(("ux", "uy", "uz", "P"), out))
+
+    def curvature(self):
+        k = np.zeros(self.shape)
+        lib().orc3_curvature(self._h, _ptr(k))
+        return k
+
+    def flow_pops(self):
+        g = np.zeros((27,) + self.shape)
+        lib().orc3_get_flow_pops(self._h, _ptr(g))
+        return g
 
     def set_pops(self, f=None, h=None):
         a = [_arr(v) for v in (f, h)]

@@ -26,6 +26,15 @@ typedef struct {
     int nx, ny, nz, pad_;
     double W, phi_a, phi_b;
     double M_phi, D_s;
+    /* The flow lattice (mode = 1): the pressure-based two-fluid flow of App. D
+     * on D3Q27, forced by the capillary and Marangoni stress of Eq. (Fs). */
+    int mode;           /* 0: prescribed velocity, f + h only; 1: coupled f + h + g */
+    int walls_y;        /* 1: half-way bounce-back walls at y = 0 (-u_wall) and y = ny (+u_wall), x-directed */
+    int sigma_literal;  /* 1: surface-tension force as printed; 0: scaled by 3W / (2 (phi_a - phi_b)^2) */
+    int pad2_;
+    double u_wall, nu_a, nu_b, zeta, rho_a, rho_b;
+    double sigma_o, beta, c_max;
+    double fext[3];
 } orc3_params;
 
 typedef struct orc3_sim orc3_sim;
@@ -36,6 +45,10 @@ void orc3_destroy(orc3_sim *s);
  * flux terms of the given phi and c); u is the prescribed velocity. */
 int orc3_init(orc3_sim *s, const double *phi, const double *c, const double *ux,
               const double *uy, const double *uz);
+/* The same with the flow lattice's initial pressure P (mode 1; NULL: the
+ * uniform rest pressure cs^2 (rho_a + rho_b) / 2). */
+int orc3_init_pressure(orc3_sim *s, const double *phi, const double *c, const double *ux,
+                       const double *uy, const double *uz, const double *P);
 void orc3_step(orc3_sim *s, int nsteps);
 long long orc3_get_step(const orc3_sim *s);
 /* phi = sum f and c = sum h of the current populations (either may be NULL). */
@@ -43,6 +56,13 @@ void orc3_fields(orc3_sim *s, double *phi, double *c);
 /* Unit normal of the current phi (components may be NULL). */
 void orc3_normals(orc3_sim *s, double *nx_, double *ny_, double *nz_);
 void orc3_get_pops(const orc3_sim *s, double *f, double *h);
+/* Flow lattice (mode 1): velocity and pressure of the current state, as the
+ * macroscopic update of App. D defines them (any output may be NULL), and
+ * the populations g. */
+void orc3_flow_fields(orc3_sim *s, double *ux, double *uy, double *uz, double *P);
+void orc3_get_flow_pops(const orc3_sim *s, double *g);
+/* Curvature kappa = div n of the current phi (the stencil of the gradient). */
+void orc3_curvature(orc3_sim *s, double *kappa);
 /* Replace the post-streaming populations (NULL leaves that lattice unchanged). */
 void orc3_set_pops(orc3_sim *s, const double *f, const double *h);
 /* The 27 velocities, e[3 * a + axis]. */

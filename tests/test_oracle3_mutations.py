@@ -4,7 +4,9 @@ Each case copies the oracle package into a temporary directory, plants one
 plausible mistake in the copy's lbm_oracle3.c (a wrong weight, a dropped or
 mis-scaled term, a flipped sign, a wrong relaxation), builds the copy and runs
 the pin meant to catch it, which must then fail.  The oracle under oracle/ is
-never modified.
+never modified.  The second half of the list plants mistakes in the flow
+lattice (equilibrium, trace and relaxation, sources, walls, forces,
+curvature).
 """
 import importlib.util
 import os
@@ -13,6 +15,7 @@ import sys
 
 import pytest
 
+import test_oracle3_flow_pins as fpins
 import test_oracle3_pins as pins
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -38,6 +41,7 @@ def _build_variant(tmp_root, tag, old, new):
 
 def _run_pin(monkeypatch, mod, pin, *args):
     monkeypatch.setattr(pins, "oracle", mod)
+    monkeypatch.setattr(fpins, "oracle", mod)
     pin(*args)
 
 
@@ -66,6 +70,27 @@ MUTATIONS = [
     ("mobility_for_surfactant", "const double w_chi = rate_from_coeff(p->D_s);",
      "const double w_chi = rate_from_coeff(p->M_phi);",
      pins.test_sphere_surface_mode_decay, (1,)),
+    # the flow lattice
+    ("flow_eq_psi_sign", "m == 1 ? -u[ax] : CS2 + u[ax] * u[ax];", "m == 1 ? u[ax] : CS2 + u[ax] * u[ax];",
+     fpins.test_flow_equilibrium_raw_moments, ()),
+    ("trace_without_m002", "B[a][a] = 1.0;  B[a][b] = 1.0;  B[a][c] = 1.0;",
+     "B[a][a] = 1.0;  B[a][b] = 1.0;  B[a][c] = 0.0;", fpins.test_sound_wave_in_three_dimensions, ()),
+    ("trace_relaxed_with_nu", "if (k == 2) lam = w_zeta;", "if (k == 2) lam = w_nu;",
+     fpins.test_sound_wave_in_three_dimensions, ()),
+    ("first_order_source_sign", "sg[first[a]] = CS2 * Ft[a] - u[a] * G;",
+     "sg[first[a]] = CS2 * Ft[a] + u[a] * G;", fpins.test_flow_reduces_to_the_2d_coupled_oracle, ("z",)),
+    ("moving_wall_term", "2.0 * weight(a) * s->rho[x] * (E3[a][0] * uw)",
+     "1.0 * weight(a) * s->rho[x] * (E3[a][0] * uw)", fpins.test_flow_reduces_to_the_2d_coupled_oracle, ("z",)),
+    ("marangoni_projection", "(gs[ax] - n[ax] * nds)", "(gs[ax])",
+     fpins.test_flow_reduces_to_the_2d_coupled_oracle, ("z",)),
+    ("curvature_without_z", "acc += weight(q) * (E3[q][0] * n[0] + E3[q][1] * n[1] + E3[q][2] * n[2]);",
+     "acc += weight(q) * (E3[q][0] * n[0] + E3[q][1] * n[1]);", fpins.test_curvature_of_sphere_and_cylinder, ()),
+    ("half_force_in_velocity", "u[ax] = (s->jv[ax][x] + 0.5 * CS2 * s->Ft[ax][x]) / (CS2 * rho);",
+     "u[ax] = (s->jv[ax][x] + 1.0 * CS2 * s->Ft[ax][x]) / (CS2 * rho);",
+     fpins.test_flow_reduces_to_the_2d_coupled_oracle, ("z",)),
+    ("xz_shear_at_rate_one", "if (k == 6 || k == 18 || k == 4 || k == 10 || k == 12) lam = w_nu;",
+     "if (k == 6 || k == 18 || k == 4 || k == 12) lam = w_nu;",
+     fpins.test_flow_reduces_to_the_2d_coupled_oracle, ("y",)),
 ]
 
 
