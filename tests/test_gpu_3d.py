@@ -10,10 +10,12 @@ collision in FP32.  Tolerances against FP64:
   * c and the h populations to the same bounds where the interface normal is
     defined, |grad phi| > 1e-5.  Far from the drop grad phi is of the order
     of the rounding of phi itself (1e-8 and below), so n there -- and with it
-    the confining flux that moves the little surfactant found there -- is set
-    by rounding, in the FP64 oracle as much as here: a perturbation of phi of
-    1e-9 turns it.  There the result is not unique, and the test asks only
-    that the difference stay below the oracle's own c in that region;
+    the confining flux that moves the little surfactant found there --
+    follows the smallest changes of phi: a perturbation of phi the size of
+    this path's own phi error (3e-7) moves the far-field c of the FP64 oracle
+    by a third of its value (an oracle-only CPU test pins this).  There the
+    result is not unique at FP32 precision, and the test asks only that the
+    difference stay below the oracle's own c in that region;
   * the initial equilibria within 1e-8 (one rounding to the 2^-28 grid);
   * sum phi and sum c exactly conserved (integer arithmetic).
 Launch shapes change only which block updates a cell, not its arithmetic, so

@@ -161,3 +161,30 @@ def test_conservation_under_a_nonuniform_velocity():
     assert np.abs(s1["phi"] - s0["phi"]).max() > 1e-3
     for name in ("phi", "c"):
         assert abs(s1[name].sum() - s0[name].sum()) < 1e-11 * abs(s0[name].sum())
+
+
+def test_far_field_surfactant_is_set_by_the_rounding_of_phi():
+    """Where |grad phi| is at the rounding level of phi (far from the drop)
+    the normal, and the confining flux that moves the little surfactant
+    there, follow the smallest changes of phi.  A random perturbation of phi
+    of 3e-7 -- the size of an FP32-arithmetic path's own phi error -- moves
+    the far-field c by a sizeable part of its value, while c where the normal
+    is defined (|grad phi| > 1e-5) moves by about the perturbation, relative.
+    This is what makes the far-field c not unique at FP32 precision."""
+    n = 32
+    case = wl.sphere_surface_mode(n=n, R=8.0, W=3.0, D_s=0.1, M_phi=0.05, mode=1,
+                                  u=(0.02, -0.013, 0.009), steps=200)
+    pert = 3e-7 * np.random.default_rng(5).standard_normal(case.phi.shape)
+    out = []
+    for phi in (case.phi, case.phi + pert):
+        s = oracle.Sim3(n, n, n, W=case.W, M_phi=case.M_phi, D_s=case.D_s)
+        s.init(phi, case.c, *case.u)
+        s.step(case.steps)
+        f = s.fields()
+        g = s.gradient(f["phi"])
+        out.append((f["c"], np.sqrt(g[0] ** 2 + g[1] ** 2 + g[2] ** 2)))
+    (ca, ga), (cb, _) = out
+    m = ga > 1e-5
+    dc = cb - ca
+    assert np.linalg.norm(dc[m]) < 1e-6 * np.linalg.norm(ca[m])
+    assert np.abs(dc[~m]).max() > 0.1 * np.abs(ca[~m]).max()
