@@ -8,7 +8,6 @@ import re
 import subprocess
 import tempfile
 
-import numpy as np
 import pytest
 
 from paper_2504_09024_gb300 import build as B
