@@ -12,7 +12,9 @@ axes by the product rule (the readings are in oracle/lbm_oracle3.c).
     k^2 / 2, the three-dimensional Chapman-Enskog result for a trace relaxed
     with zeta = cs2 (1/w - 1/2) (the 2-D rate (nu + zeta) k^2 / 2 is rejected);
   * Poiseuille flow between resting walls at nu != zeta;
-  * the curvature div n: -2/R on a sphere, -1/R on a cylinder.
+  * the curvature div n: -2/R on a sphere, -1/R on a cylinder;
+  * a spherical drop in a diagonal stream translates with it, stays
+    spherical and keeps the 3-D Laplace jump 2 sigma / R.
 """
 import math
 
@@ -190,3 +192,42 @@ def test_curvature_of_sphere_and_cylinder():
     r2 = np.hypot(X2 - n / 2, Y2 - n / 2)
     b2 = np.abs(r2 - R) < 0.5
     assert abs((kap2[b2] * r2[b2]).mean() + 1.0) < 0.01
+
+
+def test_translating_sphere():
+    """A clean spherical drop in a uniform diagonal stream (all three axes
+    active) translates with it, stays spherical and keeps the 3-D Laplace
+    jump 2 sigma / R (times the discrete tension factor of the profile)."""
+    from test_oracle_pins import _discrete_tension_factor
+    n, R, Wd, sig, T = 20, 5.0, 3.0, 1e-3, 200
+    U = (0.02, 0.015, -0.01)
+    phi, c = W.sphere_fields(n, n, n, R, Wd)
+    s = oracle.Sim3(n, n, n, W=Wd, M_phi=0.05, D_s=0.1, flow=True, nu_a=1.0 / 6.0,
+                    nu_b=1.0 / 6.0, zeta=0.5, sigma_o=sig)
+    s.init(phi, c, *U, P=CS2 + 2 * sig / R * phi)
+    X, Y, Z = W.cell_centres3(n, n, n)
+
+    def centroid(ph):
+        w = np.clip(ph, 0, 1)
+        out = []
+        for A in (X, Y, Z):
+            ang = 2 * np.pi * A / n
+            out.append((np.arctan2((w * np.sin(ang)).sum(), (w * np.cos(ang)).sum()) * n
+                        / (2 * np.pi)) % n)
+        return np.array(out)
+
+    c0 = centroid(s.fields()["phi"])
+    s.step(T)
+    ph = s.fields()["phi"]
+    c1 = centroid(ph)
+    moved = (c1 - c0 + n / 2) % n - n / 2
+    assert np.abs(moved - np.array(U) * T).max() < 1e-3 * 0.02 * T
+    d = [((A - cc + n / 2) % n) - n / 2 for A, cc in zip((X, Y, Z), c1)]
+    w = np.clip(ph, 0, 1)
+    M = np.array([[(w * d[i] * d[j]).sum() for j in range(3)] for i in range(3)]) / w.sum()
+    ev = np.linalg.eigvalsh(M)
+    assert (ev.max() - ev.min()) / ev.mean() < 1e-4
+    r = np.sqrt(d[0] ** 2 + d[1] ** 2 + d[2] ** 2)
+    P = s.flow_fields()["P"]
+    dP = P[r < R - 3].mean() - P[r > R + 4].mean()
+    assert abs(dP * R / (2 * sig * _discrete_tension_factor(Wd)) - 1) < 0.06
